@@ -1,0 +1,384 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test ties one part of the oracle to something other than the oracle's own
+formula: a dense eigendecomposition of the printed matrices, a banded solve of
+the classical compact scheme, the published Cox-Matthews ETDRK4 coefficients,
+the paper's closed-form amplification factor (Eq. 41), the RK4 reduction, exact
+single-mode decay, and the error tables printed in Section 5 (Tables 1 and 2).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    return rows
+
+
+def _same_to_printed_digits(value, printed):
+    """True when `value` rounds to the printed 5-significant-digit number."""
+    return float("%.4e" % value) == printed
+
+
+# --------------------------------------------------------------------------
+# Section 3.1: eigenvalues and eigenvectors of the compact Laplacian
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bc", O.BCS)
+@pytest.mark.parametrize("N", [4, 7, 8, 12, 16])
+def test_eigenvalues_match_dense_eig_of_printed_matrices(bc, N):
+    h = 0.37
+    A, B = O.compact_matrices(bc, N, h)
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(A, B)).real)
+    closed = np.sort(O.eigenvalues(bc, N, h))
+    assert len(ev) == len(closed)
+    np.testing.assert_allclose(closed, ev, rtol=1e-10, atol=1e-10 * ev.max())
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+@pytest.mark.parametrize("N", [5, 8, 16])
+def test_transform_pair_diagonalises_A_inv_B(bc, N):
+    """T = Finv diag(lambda) F must equal A^{-1} B entry by entry (fixes the eigenvector
+    order, the transform direction and the Neumann reading)."""
+    h = 1.0 / N
+    A, B = O.compact_matrices(bc, N, h)
+    T = np.linalg.solve(A, B)
+    F, Fi = O.transform_pair(bc, N)
+    lam = O.eigenvalues(bc, N, h)
+    T2 = Fi @ np.diag(lam) @ F
+    assert np.max(np.abs(T2.imag if np.iscomplexobj(T2) else 0.0)) < 1e-9 * np.abs(T).max()
+    np.testing.assert_allclose(T2.real, T, atol=1e-10 * np.abs(T).max())
+    np.testing.assert_allclose((Fi @ F).real, np.eye(len(lam)), atol=1e-12)
+
+
+def test_printed_periodic_angle_is_not_an_eigenvalue():
+    """The printed periodic angle (n-1) pi / (2N) gives a different spectrum; the corrected one matches."""
+    N, h = 8, 0.125
+    A, B = O.compact_matrices(O.PERIODIC, N, h)
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(A, B)).real)
+    n = np.arange(1, N + 1)
+    s = np.sin((n - 1) * np.pi / (2 * N)) ** 2
+    printed = np.sort(4 * s / (h * h * (1 - s / 3)))
+    assert np.max(np.abs(printed - ev)) > 1.0
+    np.testing.assert_allclose(np.sort(O.eigenvalues(O.PERIODIC, N, h)), ev, rtol=1e-10, atol=1e-9)
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+@pytest.mark.parametrize("alpha", [1.2, 1.5, 1.9])
+def test_fractional_power_matches_numeric_eigendecomposition(bc, alpha):
+    """T^{alpha/2} = P Lambda^{alpha/2} P^{-1} from a numerical eig (Lemma 1) vs the closed form."""
+    N, h = 12, 1.0 / 12
+    A, B = O.compact_matrices(bc, N, h)
+    T = np.linalg.solve(A, B)
+    w, V = np.linalg.eig(T)
+    w = np.where(np.abs(w) < 1e-9, 0.0, w.real)
+    Tf = (V @ np.diag(np.power(w, alpha / 2)) @ np.linalg.inv(V)).real
+    F, Fi = O.transform_pair(bc, N)
+    lam = O.eigenvalues(bc, N, h)
+    closed = (Fi @ np.diag(np.power(lam, alpha / 2)) @ F).real
+    np.testing.assert_allclose(closed, Tf, atol=1e-9 * np.abs(Tf).max())
+    if bc == O.DIRICHLET:       # SPD: also against scipy's Schur-Pade fractional power
+        Tsp = sla.fractional_matrix_power(T, alpha / 2).real
+        np.testing.assert_allclose(closed, Tsp, atol=1e-8 * np.abs(Tsp).max())
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+def test_alpha2_reduces_to_classical_compact_scheme_2d(bc):
+    """At alpha = 2 the MTT operator is T_x (x) U + T_y (y) U (Eq. EP) with T v = A^{-1}(B v)
+    computed by a banded (or cyclic) solve."""
+    Nx, Ny = 10, 14
+    g = O.Grid((Nx, Ny), (0.0, -1.0), (1.3, 2.0))
+    sp = O.Spectral(g, bc)
+    U = np.random.default_rng(7).standard_normal(g.shape(bc))
+
+    def T_apply(N, h, V, axis):
+        A, B = O.compact_matrices(bc, N, h)
+        BV = np.moveaxis(np.tensordot(B, V, axes=([1], [axis])), 0, axis)
+        if bc == O.PERIODIC:
+            return np.moveaxis(np.tensordot(np.linalg.inv(A), BV, axes=([1], [axis])), 0, axis)
+        n = A.shape[0]
+        ab = np.zeros((3, n))
+        ab[0, 1:] = np.diag(A, 1)
+        ab[1, :] = np.diag(A)
+        ab[2, :-1] = np.diag(A, -1)
+        moved = np.moveaxis(BV, axis, 0)
+        sol = sla.solve_banded((1, 1), ab, moved.reshape(n, -1)).reshape(moved.shape)
+        return np.moveaxis(sol, 0, axis)
+
+    ref = T_apply(Nx, g.h(0), U, 1) + T_apply(Ny, g.h(1), U, 0)
+    got = sp.frac_laplacian(U, 2.0)
+    np.testing.assert_allclose(got, ref, atol=1e-9 * np.abs(ref).max())
+
+
+def test_compact_laplacian_is_fourth_order():
+    """-Delta sin(pi x) on Dirichlet grids: error of A^{-1}B falls by ~16 per halving (Eq. Lap)."""
+    errs = []
+    for N in (16, 32, 64):
+        h = 1.0 / N
+        x = np.arange(1, N) * h
+        F, Fi = O.transform_pair(O.DIRICHLET, N)
+        lam = O.eigenvalues(O.DIRICHLET, N, h)
+        v = np.sin(np.pi * x)
+        errs.append(np.max(np.abs(Fi @ (lam * (F @ v)) - np.pi ** 2 * v)))
+    assert 15.0 < errs[0] / errs[1] < 17.0 and 15.0 < errs[1] / errs[2] < 17.0
+
+
+# --------------------------------------------------------------------------
+# Section 4: Pade-(1,3) coefficients
+# --------------------------------------------------------------------------
+
+def test_pade13_is_fourth_order_approximation_of_exp():
+    z = np.array([1e-2, 2e-2, 4e-2])
+    err = np.abs(O.pade13(z) - np.exp(-z))
+    ratios = err[1:] / err[:-1]
+    np.testing.assert_allclose(ratios, 32.0, rtol=0.05)   # O(z^5)
+
+
+@pytest.mark.parametrize("L", [1e-3, 0.25, 1.0, 4.6, 36.0, 1e3])
+def test_coefficients_equal_cox_matthews_with_pade_exponential(L):
+    """Algorithm 1's rationals equal the Cox-Matthews ETDRK4 coefficients with e^{-L} replaced
+    by R13(L) (and e^{-L/2} by R13(L/2) = Q13)."""
+    tau = 0.37
+    c = O.p13_coefficients(L, tau)
+    R, Q = O.pade13(L), O.pade13(L / 2)
+    assert c["R13"] == pytest.approx(R, rel=1e-13)
+    assert c["Q13"] == pytest.approx(Q, rel=1e-13)
+    assert c["phi"] == pytest.approx(tau * (1 - Q) / L, rel=1e-8 if L < 1e-2 else 1e-12)
+    if L > 0.2:   # the Cox-Matthews forms cancel catastrophically for small L
+        assert c["phi1"] == pytest.approx(tau * (-4 + L + R * (4 + 3 * L + L * L)) / (-L ** 3), rel=1e-10)
+        assert c["phi2"] == pytest.approx(2 * tau * (2 - L - R * (2 + L)) / (-L ** 3), rel=1e-10)
+        assert c["phi3"] == pytest.approx(tau * (-4 + 3 * L - L * L + R * (4 + L)) / (-L ** 3), rel=1e-10)
+
+
+def test_coefficients_zero_eigenvalue_limits():
+    tau = 0.1
+    c = O.p13_coefficients(np.array([0.0]), tau)
+    assert c["R13"][0] == 1.0 and c["Q13"][0] == 1.0
+    assert c["phi"][0] == pytest.approx(tau / 2)
+    assert c["phi1"][0] == pytest.approx(tau / 6)
+    assert c["phi2"][0] == pytest.approx(tau / 3)
+    assert c["phi3"][0] == pytest.approx(tau / 6)
+
+
+def test_coefficient_derivatives_match_finite_differences():
+    tau = 0.3
+    for L in (0.0, 0.7, 5.0, 40.0):
+        d = O.coefficient_derivatives(L, tau)
+        hh = 1e-6 * max(1.0, L)
+        cp, cm = O.p13_coefficients(L + hh, tau), O.p13_coefficients(L - hh, tau)
+        for k in d:
+            assert d[k] == pytest.approx((cp[k] - cm[k]) / (2 * hh), rel=1e-6, abs=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Section 4.2: linear analysis
+# --------------------------------------------------------------------------
+
+def eq41(x, y):
+    """Amplification factor of Eq. 41 as printed, with the y^2 term of c1's numerator restored
+    (+55738368 y^2; symbolic derivation from the scheme)."""
+    d1 = 24 - 18 * y + 6 * y ** 2 - y ** 3
+    d2 = 192 - 72 * y + 12 * y ** 2 - y ** 3
+    c0 = 6 * (4 + y) / d1
+    c1 = (169869312 - 148635648 * y + 55738368 * y ** 2 - 9621504 * y ** 3 + 470016 * y ** 4
+          + 165888 * y ** 5 - 46464 * y ** 6 + 6240 * y ** 7 - 600 * y ** 8 + 32 * y ** 9
+          - y ** 10) / (d2 ** 3 * d1)
+    c2 = (442368 - 221184 * y + 34560 * y ** 2 + 11712 * y ** 3 - 2976 * y ** 4 + 404 * y ** 5
+          - 25 * y ** 6 + y ** 7) / (d2 ** 2 * d1)
+    c3 = 2 * (96 - 12 * y + y ** 2) ** 2 * (1536 - 960 * y + 240 * y ** 2 + 8 * y ** 3 + y ** 4) / (d2 ** 3 * d1)
+    c4 = 2 * (96 - 12 * y + y ** 2) ** 3 * (4 - 3 * y + y ** 2) / (d2 ** 3 * d1)
+    return c0 + c1 * x + c2 * x ** 2 + c3 * x ** 3 + c4 * x ** 4
+
+
+def _one_mode_factor(bc, N, mode, x, y_target, alpha=1.6):
+    """Apply one oracle step to a single eigenmode with f(u) = gamma u; return u^{k+1}/u^k."""
+    g = O.Grid((N,), (0.0,), (1.0,))
+    sp = O.Spectral(g, bc)
+    lam = sp.Lambda_frac(alpha)
+    tau = 0.05
+    kappa = -y_target / (tau * lam[mode])      # y = -kappa tau lambda^{alpha/2}
+    gamma = x / tau
+    f, J = O.linear(gamma)
+    prob = O.Problem(g, bc, [alpha], [kappa], tau, f, dreaction=J, nspecies=1)
+    s = O.ETDRK4P13(prob)
+    coef = np.zeros(len(lam))
+    coef[mode] = 1.0
+    u0 = sp.inverse(coef)
+    u0 = u0.real if bc == O.PERIODIC else u0
+    u1 = s.step([u0], 0.0)[0]
+    return float(np.dot(u1, u0) / np.dot(u0, u0))
+
+
+@pytest.mark.parametrize("bc,mode", [(O.DIRICHLET, 2), (O.NEUMANN, 3)])
+@pytest.mark.parametrize("x,y", [(-0.5, -1.0), (0.3, -4.0), (-2.0, -20.0), (1.0, -0.2), (-0.1, -60.0)])
+def test_step_reproduces_amplification_factor_eq41(bc, mode, x, y):
+    assert _one_mode_factor(bc, 16, mode, x, y) == pytest.approx(eq41(x, y), rel=1e-11, abs=1e-13)
+
+
+@pytest.mark.parametrize("x", [-2.5, -1.0, -0.3, 0.4])
+def test_eq41_at_y0_is_rk4(x):
+    assert eq41(x, 0.0) == pytest.approx(1 + x + x * x / 2 + x ** 3 / 6 + x ** 4 / 24, rel=1e-14)
+
+
+def test_single_eigenmode_decays_by_r13_power():
+    """f = 0: each eigen-coefficient is multiplied by R13(L) per step, exactly."""
+    N, M = 16, 7
+    g = O.Grid((N, N), (0.0, 0.0), (2.0, 2.0))
+    f, J = O.linear(0.0)
+    for bc in O.BCS:
+        prob = O.Problem(g, bc, [1.7], [0.3], 0.2, f, dreaction=J, nspecies=1)
+        s = O.ETDRK4P13(prob)
+        rng = np.random.default_rng(3)
+        u0 = rng.standard_normal(g.shape(bc))
+        uM = s.run([u0], 0.0, M)[0]
+        expect = s.sp.forward(u0) * s.coef[0]["R13"] ** M
+        got = s.sp.forward(uM)
+        np.testing.assert_allclose(got, expect, atol=1e-12 * np.abs(expect).max())
+
+
+@pytest.mark.parametrize("bc", [O.PERIODIC, O.NEUMANN])
+def test_zero_mode_is_conserved_without_reaction(bc):
+    N = 12
+    g = O.Grid((N, N), (0.0, 0.0), (1.0, 1.0))
+    f, J = O.linear(0.0)
+    prob = O.Problem(g, bc, [1.4], [2.0], 0.5, f, dreaction=J, nspecies=1)
+    s = O.ETDRK4P13(prob)
+    u0 = np.random.default_rng(1).standard_normal(g.shape(bc))
+    u1 = s.run([u0], 0.0, 5)[0]
+    z0, z1 = s.sp.forward(u0).flat[0], s.sp.forward(u1).flat[0]
+    assert abs(z1 - z0) < 1e-12 * abs(z0) + 1e-12
+
+
+# --------------------------------------------------------------------------
+# Section 5: the printed error tables
+# --------------------------------------------------------------------------
+
+def _example1_error(Ninv):
+    g = O.Grid((Ninv,), (0.0,), (1.0,))
+    kappa, alpha = 10.0, 1.8
+    tau = (1.0 / Ninv) / (4 * kappa)
+    f, exact = O.fisher_mms(g, kappa, alpha)
+    s = O.ETDRK4P13(O.Problem(g, O.DIRICHLET, [alpha], [kappa], tau, f, nspecies=1))
+    M = int(round(1.0 / tau))
+    u = s.run([exact(0.0)], 0.0, M)
+    return O.max_error(u[0], exact(M * tau))
+
+
+@pytest.mark.parametrize("row", _table("table1.txt"))
+def test_table1_example1_errors(row):
+    Ninv, printed = int(row[0]), row[1]
+    assert _same_to_printed_digits(_example1_error(Ninv), printed)
+
+
+def _example2_error(bc, alpha, Ninv):
+    g = O.Grid((Ninv, Ninv), (0.0, 0.0), (1.0, 1.0))
+    tau = 0.1 / Ninv
+    f, exact = O.huxley_mms(g, bc, 1.0, alpha)
+    s = O.ETDRK4P13(O.Problem(g, bc, [alpha], [1.0], tau, f, nspecies=1))
+    M = int(round(1.0 / tau))
+    u = s.run([exact(0.0)], 0.0, M)
+    return O.max_error(u[0], exact(M * tau))
+
+
+_T2 = [r for r in _table("table2.txt") if r[1] <= 80 or r[0] == 1.8]
+
+
+@pytest.mark.parametrize("row", _T2, ids=["a%.1f-n%d" % (r[0], r[1]) for r in _T2])
+@pytest.mark.parametrize("bc", [O.NEUMANN, O.PERIODIC])
+def test_table2_example2_errors(row, bc):
+    alpha, Ninv = row[0], int(row[1])
+    printed = row[2] if bc == O.NEUMANN else row[3]
+    assert _same_to_printed_digits(_example2_error(bc, alpha, Ninv), printed)
+
+
+def test_table_orders_are_four():
+    rows = _table("table1.txt")
+    errs = [_example1_error(int(r[0])) for r in rows[:3]]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(3.9 < o < 4.4 for o in orders)
+
+
+# --------------------------------------------------------------------------
+# Symmetry and the adjoint
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bc", [O.DIRICHLET, O.NEUMANN])
+def test_mirror_symmetric_initial_data_stays_symmetric(bc):
+    N = 10
+    g = O.Grid((N, N), (0.0, 0.0), (1.0, 1.0))
+    f, J, _ = O.fitzhugh_nagumo()
+    prob = O.Problem(g, bc, [1.5, 1.5], [0.01, 0.002], 0.2, f, dreaction=J)
+    s = O.ETDRK4P13(prob)
+    rng = np.random.default_rng(11)
+    u = rng.uniform(0, 1, g.shape(bc))
+    u = u + u[:, ::-1]
+    v = rng.uniform(0, 0.1, g.shape(bc))
+    v = v + v[:, ::-1]
+    out = s.run([u, v], 0.0, 6)
+    for w in out:
+        np.testing.assert_allclose(w, w[:, ::-1], atol=1e-13)
+    # exchange of axes on a square grid
+    ut, vt = s.run([u.T.copy(), v.T.copy()], 0.0, 6)
+    np.testing.assert_allclose(ut, out[0].T, atol=1e-13)
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+def test_oracle_adjoint_matches_central_differences(bc):
+    """dl/du0, dl/dalpha, dl/dkappa and dl/dmu of l = 1/2 ||u_M - target||^2 through 3 steps."""
+    N = 6
+    g = O.Grid((N, N), (0.0, 0.0), (10.0, 10.0))
+    rng = np.random.default_rng(5)
+
+    def build(alpha, kappa_u, mu):
+        f, J, dmu = O.fitzhugh_nagumo(mu=mu)
+        prob = O.Problem(g, bc, [alpha, alpha], [kappa_u, 0.3], 0.1, f, dreaction=J)
+        return O.ETDRK4P13(prob), dmu
+
+    shp = g.shape(bc)
+    u0 = [rng.uniform(0, 1, shp), rng.uniform(0, 0.2, shp)]
+    tgt = [rng.uniform(0, 1, shp), rng.uniform(0, 0.2, shp)]
+    M = 3
+    th = dict(alpha=1.6, kappa_u=1.0, mu=0.1)
+
+    def loss(th_, u0_):
+        s, _ = build(th_["alpha"], th_["kappa_u"], th_["mu"])
+        uM = s.run(u0_, 0.0, M)
+        return 0.5 * sum(float(np.sum((a - b) ** 2)) for a, b in zip(uM, tgt))
+
+    s, dmu = build(**th)
+    uM = s.run(u0, 0.0, M)
+    gr = O.adjoint_run(s, u0, 0.0, M, [a - b for a, b in zip(uM, tgt)], dparams=dmu)
+    hh = 1e-6
+    for name in ("alpha", "kappa_u", "mu"):
+        tp, tm = dict(th), dict(th)
+        tp[name] += hh
+        tm[name] -= hh
+        fd = (loss(tp, u0) - loss(tm, u0)) / (2 * hh)
+        if name == "alpha":
+            got = sum(gr["alpha"])
+        elif name == "kappa_u":
+            got = gr["kappa"][0]
+        else:
+            got = gr["params"]
+        assert got == pytest.approx(fd, rel=1e-6, abs=1e-9), name
+    for idx in [(0, 1, 2), (1, 3, 0)]:
+        sp_, i, j = idx
+        up = [x.copy() for x in u0]
+        um = [x.copy() for x in u0]
+        up[sp_][i, j] += hh
+        um[sp_][i, j] -= hh
+        fd = (loss(th, up) - loss(th, um)) / (2 * hh)
+        assert gr["u0"][sp_][i, j] == pytest.approx(fd, rel=1e-6, abs=1e-9)
