@@ -1,0 +1,326 @@
+"""Throughput of the ETDRK4-P13 time step on GB300: DOF-steps/s and HBM roofline fraction.
+
+Workload: 3D fractional Schnakenberg, homogeneous Dirichlet BC on the
+perturbation (DST-I), N = 256 intervals per axis (255^3 interior unknowns, FFT
+length 512), 2 species, alpha = 1.5, kappa = (1, 10), gamma = 1000, dt = 1e-4,
+seeded U(-0.01, 0.01) perturbation.  One bench step = one ETDRK4-P13 time step
+of the resident spectral state (all four stages: transforms, Pade-(1,3)
+combination, reaction) -- launched as the library's captured CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank advances its own replica:
+the method has no data-parallel exchange for one grid, so this is replicas-only
+weak scaling.  --impl reference times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "ETDRK4 DOF-steps/s, FP32 vs FP64, 3D 255^3, and % of HBM roofline"
+WORKLOAD = "schnak256"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_desc(cfg):
+    return ("3D fractional Schnakenberg, Dirichlet (DST-I), N=%d (%d^3 interior, FFT length %d), 2 species, "
+            "alpha=%.1f, kappa=(%g,%g), gamma=%g, dt=%g" % (cfg["N"][0], cfg["N"][0] - 1, 2 * cfg["N"][0],
+                                                            cfg["alpha"][0], cfg["kappa"][0], cfg["kappa"][1],
+                                                            cfg["reaction"]["p"][0], cfg["dt"]))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for i, nm in enumerate(names):
+                    if r[5 + i].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# Algorithmic HBM words per unknown (per species element) of each pass kind; see the design doc.
+# x pass: read + write the field (the reaction needs no extra traffic);
+# middle pass: read + write; slow passes: field in/out + stored spectra + coefficients.
+WORDS = {0: 2, 1: 2, 2: 6, 3: 6, 4: 7, 5: 11}
+KIND_NAME = {0: "x_pass_react", 1: "y_pass_middle", 2: "z_pass_stage_a", 3: "z_pass_stage_b",
+             4: "z_pass_stage_c", 5: "z_pass_update"}
+
+
+def ncu_traffic(kind_name):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if one exists for it."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 2 and parts[0] == kind_name:
+            try:
+                return float(parts[1])
+            except ValueError:
+                return None
+    return None
+
+
+def cpu_baseline(cfg, seconds):
+    """The FP64 oracle (dense per-axis transforms, Algorithm 1) timed on the host cores."""
+    from oracle.bridge import solver as oracle_solver
+    u0 = W.initial_fields(cfg)
+    s = oracle_solver(cfg)
+    t0 = time.perf_counter()
+    n = 0
+    u = u0
+    while True:
+        u = s.step(u, n * cfg["dt"])
+        n += 1
+        if time.perf_counter() - t0 > seconds or n >= 50:
+            break
+    el = time.perf_counter() - t0
+    dof = int(np.prod(W.field_shape(cfg))) * 2
+    return {"value": dof * n / el, "unit": "DOF-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d ETDRK4-P13 step(s) of the full %s workload, FP64 dense-matrix oracle, %.1f s"
+                      % (n, "x".join(str(x) for x in W.field_shape(cfg)), el)}
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle on a bounded sample of the workload per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # per step: one oracle ETDRK4 step on a reduced grid of the same workload so that
+    # the whole --steps/--warmup run stays within a few minutes
+    Nsample = int(os.environ.get("SFRD_REF_N", "64"))
+    cfg = W.scaled(WORKLOAD, Nsample)
+    from oracle.bridge import solver as oracle_solver
+    s = oracle_solver(cfg)
+    u = W.initial_fields(cfg)
+    for k in range(args.warmup):
+        u = s.step(u, k * cfg["dt"])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        u = s.step(u, k * cfg["dt"])
+    el = time.perf_counter() - t0
+    dof = int(np.prod(W.field_shape(cfg))) * 2
+    v = dof * args.steps / el
+    line = {"metric": METRIC, "value": v, "unit": "DOF-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(W.config(WORKLOAD)),
+                       "sample_grid": list(cfg["N"]), "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "DOF-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "one FP64 oracle step per bench step on the same workload at N=%d "
+                                       "(%d^3 interior)" % (Nsample, Nsample - 1)},
+            "e2e": {"value": v, "unit": "DOF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_2003_13569_gb300 as sf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cfg = W.config(WORKLOAD)
+    u0 = W.initial_fields(cfg, seed=cfg["seed"] + rank)
+    solver = sf.Solver(cfg, dtype=args.dtype)
+    dof = solver.dof
+    stream = solver.stream
+    u0_dev = torch.as_tensor(np.stack(u0)).to(device="cuda", dtype=solver.tdtype)
+    solver.load(u0_dev, 0.0)
+    solver.advance(args.warmup)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0.0)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.advance(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = dof * args.steps * world / (ms * 1e-3)
+
+    # per-launch profile of the same step (events on the launching stream)
+    prof = {}
+    nprof = max(3, min(args.steps, 10))
+    for _ in range(nprof):
+        for kd, t in solver.profile_step():
+            prof.setdefault(kd, []).append(t)
+    esize = 4 if args.dtype == "f32" else 8
+    per_kind = {}
+    tot = sum(sum(v) for v in prof.values())
+    for kd, ts in prof.items():
+        avg = sum(ts) / len(ts)
+        algo = WORDS[kd] * dof * esize
+        per_kind[KIND_NAME[kd]] = {"launches_per_step": len(ts) // nprof, "avg_ms": avg,
+                                   "share": sum(ts) / tot, "algo_bytes": algo,
+                                   "gbs": algo / (avg * 1e-3) / 1e9}
+    dom = max(per_kind.items(), key=lambda kv: kv[1]["share"])
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "achieved": dom[1]["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": dom[1]["gbs"] / peak, "traffic": ncu_traffic(dom[0]), "kernel": dom[0],
+            "peak_source": peak_kind}
+    step_words = sum(WORDS[kd] * len(ts) / nprof for kd, ts in prof.items())
+    model_bytes = step_words * dof * esize
+    step_roof = {"model_words_per_dof_step": step_words, "model_bytes_per_step": model_bytes,
+                 "achieved_gbs": model_bytes / (ms * 1e-3 / args.steps) / 1e9,
+                 "frac_of_" + peak_kind: model_bytes / (ms * 1e-3 / args.steps) / 1e9 / peak}
+
+    # FP64 path on the same workload, and the FP32-vs-FP64 error after the same steps
+    extra = {}
+    if rank == 0 and args.dtype == "f32" and args.fp64_steps > 0:
+        s64 = sf.Solver(cfg, dtype="f64")
+        s64.load(u0_dev.double(), 0.0)
+        s64.advance(1)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(s64.stream)
+        s64.advance(args.fp64_steps)
+        a1.record(s64.stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1)
+        ref = s64.run(u0_dev.double(), nsteps=args.fp64_steps)
+        got = solver.run(u0_dev, nsteps=args.fp64_steps).double()
+        err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+        extra["fp64"] = {"value": dof * args.fp64_steps / (ms64 * 1e-3), "unit": "DOF-steps/s",
+                         "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
+        extra["fp32_vs_fp64_rel_l2"] = {"value": err, "steps": args.fp64_steps}
+        del s64
+        torch.cuda.empty_cache()
+
+    # end to end through host memory: pinned input -> device -> K steps -> pinned output
+    host_in = torch.as_tensor(np.stack(u0)).to(dtype=solver.tdtype).contiguous().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    solver.run_host_ptr(host_in.data_ptr(), host_out.data_ptr(), 0.0, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    ncalls = 2
+    for _ in range(ncalls):
+        solver.run_host_ptr(host_in.data_ptr(), host_out.data_ptr(), 0.0, args.steps)
+    el = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    fbytes = host_in.numel() * host_in.element_size()
+    e2e = {"value": dof * args.steps * ncalls * world / el, "unit": "DOF-steps/s",
+           "h2d_bytes_per_step": fbytes / args.steps, "d2h_bytes_per_step": fbytes / args.steps,
+           "steps_per_call": args.steps, "api": "sfrd_run_host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "DOF-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": workload_desc(cfg), "grid_intervals": list(cfg["N"]),
+                           "unknowns": list(solver.shape), "dof": dof, "parallelism": "replicas",
+                           "l2": "inputs larger than L2 (resident state + stored spectra + coefficients "
+                                 "%.2f GB > 126 MB)" % (solver.info.workspace_bytes / 1e9),
+                           "timed": "sfrd_advance (captured CUDA graph), one ETDRK4-P13 step per bench step"},
+                "gpu_launches": solver.kernels_per_step * args.steps,
+                "roofline": roof, "step_roofline": step_roof, "kernels": per_kind,
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

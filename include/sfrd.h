@@ -1,0 +1,205 @@
+/*
+ * sfrd.h -- C ABI of the GB300 (sm_103a) compact-MTT ETDRK4-P13 solver for
+ * space-fractional reaction-diffusion equations (Bhatt et al., arXiv 2003.13569).
+ *
+ * Problem (Section 1, Eq. 1):
+ *     du_s/dt = -kappa_s (-Delta)^{alpha_s/2} u_s + f_s(u, t),   1 < alpha_s <= 2,
+ * on a box in R^d (d = 2, 3) with periodic, homogeneous Dirichlet or homogeneous
+ * Neumann boundary conditions, one to two species s.
+ *
+ * Space (Section 3): the fractional Laplacian is the matrix transfer technique
+ * applied to the fourth-order compact Laplacian T = A^{-1}B (Eqs. Lap, MTT);
+ * T is diagonalised per axis by the DFT (periodic, Eq. PP), DST-I (Dirichlet,
+ * Eq. PD) or DCT-I (Neumann, Eq. PN), and the summed eigenvalue
+ * Lambda = lambda_x + lambda_y (+ lambda_z) is raised to alpha/2 (Eqs. E16-E22).
+ * Time (Section 4, Eq. ETDRK4P13, Algorithm 1): ETDRK4 with e^{-z} replaced by
+ * its Pade-(1,3) approximant; the six coefficient arrays R13, Q13, phi, phi1,
+ * phi2, phi3 of L = kappa tau Lambda^{alpha/2} are computed once in FP64 on the
+ * GPU and stored in the run precision.
+ *
+ * Conventions shared by every call:
+ *   - Grid: N[d] = number of intervals on [lo[d], hi[d]], axes listed x, y, z.
+ *     Unknowns per axis: N (periodic: nodes 0..N-1), N-1 (Dirichlet: nodes
+ *     1..N-1), N+1 (Neumann: nodes 0..N).
+ *   - Field layout (device or host, as each call says): species-major, dense,
+ *     row-major [S][n_z][n_y][n_x] (3D) or [S][n_y][n_x] (2D), x fastest, in
+ *     the plan's dtype (double for SFRD_F64, float for SFRD_F32).
+ *   - Ownership: the caller owns every field buffer, the workspace and the
+ *     stream; the plan owns only host metadata and its CUDA graph.  Device
+ *     pointers are never freed by the library.
+ *   - Errors: every call returns SFRD_OK (0) or a negative code; nothing aborts
+ *     the process and no kernel traps.  SFRD_ECUDA carries the CUDA error
+ *     string in sfrd_last_error().
+ *   - Ordering: every device call is enqueued on the stream given to
+ *     sfrd_bind and returns without synchronising, except those whose
+ *     description says they synchronise.
+ */
+#ifndef SFRD_H
+#define SFRD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define SFRD_OK            0
+#define SFRD_EINVAL       -1  /* bad argument: alpha not in (1,2], kappa < 0, dt <= 0, N < 2, ... */
+#define SFRD_EUNSUPPORTED -2  /* valid problem outside what this build handles (length not
+                                 {2,3,5}-smooth, FFT length > 1024, dim not 2 or 3, ...) */
+#define SFRD_ENOWS        -3  /* workspace missing, too small or not bound */
+#define SFRD_ECUDA        -4  /* a CUDA runtime call failed; see sfrd_last_error() */
+#define SFRD_ENONFINITE   -5  /* a non-finite value was detected in the state */
+#define SFRD_ESTATE       -6  /* call out of order (e.g. advance before load) */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define SFRD_BC_PERIODIC   0  /* Section 3.1.1: DFT eigenvectors (Eq. PP) */
+#define SFRD_BC_DIRICHLET  1  /* Section 3.1.2: DST-I eigenvectors (Eq. PD) */
+#define SFRD_BC_NEUMANN    2  /* Section 3.1.3: DCT-I eigenvectors (Eq. PN) */
+
+#define SFRD_F64 0            /* fields, transforms and reaction in FP64 */
+#define SFRD_F32 1            /* fields, transforms and reaction in FP32; coefficients and
+                                 twiddles computed in FP64 and rounded once to FP32 */
+
+/* Reaction terms f(u, t).  p[] and offset[] meanings per kind:
+ *   NONE               f = 0                                   (1 or 2 species)
+ *   LINEAR             f_s = p0 u_s                            (Eq. TEq test equation)
+ *   FHN                p = [mu, eps, beta, gamma, delta]:      (Section 5.2, FitzHugh-Nagumo)
+ *                      f_u = u(1-u)(u-mu) - v,  f_v = eps(beta u - gamma v - delta)
+ *   GRAY_SCOTT         p = [F, K]:                             (Section 5.2, Eq. SG)
+ *                      f_u = -u v^2 + F(1-u),   f_v = u v^2 - (F+K) v
+ *   SCHNAKENBERG       p = [gamma, a, b]:                      (Section 5.2, Eq. SB)
+ *                      f_u = gamma(a - U + U^2 V), f_v = gamma(b - U^2 V)
+ *   GIERER_MEINHARDT   p = [c1, c2, c3, c4]:                   (Section 5.2, Eq. GM)
+ *                      f_u = c1 U^2/V - c2 U,   f_v = c3 U^2 - c4 V
+ *   HUXLEY_MMS         Example 2 (Section 5.1): u(1-u)(u-1) + the manufactured source
+ *                      of u = t^alpha cos^3(2 pi x) cos^3(2 pi y); 1 species, 2D.
+ * For SCHNAKENBERG and GIERER_MEINHARDT, U = u + offset[0], V = v + offset[1]:
+ * the solver integrates the perturbation about (offset[0], offset[1]); with
+ * Dirichlet BCs the boundary condition applies to that perturbation. */
+#define SFRD_REACT_NONE              0
+#define SFRD_REACT_LINEAR            1
+#define SFRD_REACT_FHN               2
+#define SFRD_REACT_GRAY_SCOTT        3
+#define SFRD_REACT_SCHNAKENBERG      4
+#define SFRD_REACT_GIERER_MEINHARDT  5
+#define SFRD_REACT_HUXLEY_MMS        6
+
+typedef struct sfrd_plan_s* sfrd_plan_t;
+
+typedef struct {
+    int32_t dim;      /* 2 or 3 */
+    int64_t N[3];     /* intervals per axis (x, y, z); unused entries ignored */
+    double  lo[3];
+    double  hi[3];
+} sfrd_grid;
+
+typedef struct {
+    int32_t kind;       /* SFRD_REACT_* */
+    int32_t nspecies;   /* 1 or 2 */
+    double  p[8];
+    double  offset[2];
+} sfrd_reaction;
+
+typedef struct {
+    int32_t dim, bc, dtype, nspecies;
+    int64_t n[3];            /* unknowns per axis (x, y, z) */
+    int64_t fft_len[3];      /* complex FFT length per axis (N periodic, 2N otherwise) */
+    int64_t dof;             /* unknowns x species */
+    int64_t kernels_per_step;/* kernel launches of one ETDRK4 step */
+    size_t  workspace_bytes;
+} sfrd_info;
+
+/* Create a plan (host only; no CUDA call).  Section 1 (Eq. 1) problem data:
+ *   grid     : box and intervals;          bc    : SFRD_BC_*;
+ *   alpha    : [nspecies] orders in (1,2]; kappa : [nspecies] diffusion >= 0;
+ *   dt       : time step tau > 0;          dtype : SFRD_F64 or SFRD_F32;
+ *   reaction : f(u, t), see above.
+ * On success *out owns a new plan (release with sfrd_destroy).
+ * Errors: SFRD_EINVAL, SFRD_EUNSUPPORTED. */
+int sfrd_plan(sfrd_plan_t* out, const sfrd_grid* grid, int32_t bc,
+              const double* alpha, const double* kappa, double dt,
+              int32_t dtype, const sfrd_reaction* reaction);
+
+/* Bytes of device workspace the plan needs (coefficient arrays, spectral state
+ * and stored stage spectra, scratch, tables). */
+int sfrd_workspace_bytes(sfrd_plan_t plan, size_t* bytes);
+
+/* Static description of the plan (sizes, launches per step). */
+int sfrd_get_info(sfrd_plan_t plan, sfrd_info* info);
+
+/* Attach caller-owned device workspace (>= sfrd_workspace_bytes, 256-byte
+ * aligned) and a cudaStream_t (NULL = legacy default stream).  Uploads the
+ * FP64-computed eigenvalue, twiddle and permutation tables and runs the FP64
+ * init kernel that fills the six Algorithm 1 coefficient arrays (Algorithm 1,
+ * precompute lines).  May be called again to move the plan to new memory or a
+ * new stream; the resident state is then invalid until the next sfrd_load.
+ * Errors: SFRD_ENOWS (NULL, short or misaligned workspace), SFRD_ECUDA. */
+int sfrd_bind(sfrd_plan_t plan, void* workspace, size_t bytes, void* stream);
+
+/* Transform a physical device field u0 [S][...] to the resident spectral state
+ * (Algorithm 1: u_h = fftn(u)) and set the clock to t0.  u0 is only read. */
+int sfrd_load(sfrd_plan_t plan, const void* u0, double t0);
+
+/* Advance the resident state by nsteps ETDRK4-P13 steps (Eq. ETDRK4P13;
+ * Algorithm 1 loop body, four stages with reaction times t_k, t_k + tau/2,
+ * t_k + tau/2, t_k + tau).  Launched as a captured CUDA graph.  nsteps >= 0. */
+int sfrd_advance(sfrd_plan_t plan, int64_t nsteps);
+
+/* Write the resident state to the physical device field u [S][...]
+ * (Algorithm 1: u = ifftn(...)).  Does not change the resident state. */
+int sfrd_store(sfrd_plan_t plan, void* u);
+
+/* u <- u(t0 + nsteps tau): sfrd_load(u, t0); sfrd_advance(nsteps); sfrd_store(u).
+ * u is a device field, overwritten in place. */
+int sfrd_run(sfrd_plan_t plan, void* u, double t0, int64_t nsteps);
+
+/* One step: sfrd_run(plan, u, t, 1). */
+int sfrd_step(sfrd_plan_t plan, void* u, double t);
+
+/* End-to-end run through host memory: copies u_in (host, [S][...]) to the
+ * device, runs nsteps from t0, copies the result to u_out (host, may equal
+ * u_in) and synchronises the stream.  Pinned host buffers give overlap-free
+ * DMA at full speed; pageable buffers work but are slower. */
+int sfrd_run_host(sfrd_plan_t plan, const void* u_in, void* u_out, double t0, int64_t nsteps);
+
+/* The separable transform of Eqs. E19/E22 in this library's real form:
+ * uhat = T_z T_y T_x u with T = discrete Hartley transform (periodic; it shares
+ * the DFT's eigenvalues because lambda_k = lambda_{N-k}), DST-I (Dirichlet) or
+ * DCT-I with endpoint weights (1/2, 1, ..., 1, 1/2) on the input (Neumann),
+ * all unnormalised.  u and uhat are dense device fields [S][...]. */
+int sfrd_forward(sfrd_plan_t plan, const void* u, void* uhat);
+
+/* Inverse of sfrd_forward: u = T_z T_y T_x uhat / C with C = prod over axes of
+ * (N for periodic, N/2 otherwise). */
+int sfrd_inverse(sfrd_plan_t plan, const void* uhat, void* u);
+
+/* Copy coefficient array `which` (0 R13, 1 Q13, 2 phi, 3 phi1, 4 phi2, 5 phi3;
+ * Algorithm 1) for every species into the dense device buffer out [S][...],
+ * indexed like the spectral field (mode k per axis in eigenvalue order). */
+int sfrd_coefficients(sfrd_plan_t plan, int32_t which, void* out);
+
+/* Per-launch device times of one ETDRK4 step of the resident state (which it
+ * advances): the step's kernels are launched individually (no graph) with a
+ * CUDA event recorded on the bound stream before and after each launch; the
+ * call synchronises.  For i < min(cap, kernels_per_step): ms[i] = duration of
+ * launch i, kind[i] = pass kind (0: contiguous-axis pass with the reaction,
+ * 1: middle-axis pass, 2..5: slow-axis pass of stage a, b, c, update).
+ * Errors: SFRD_ESTATE before sfrd_load. */
+int sfrd_profile_step(sfrd_plan_t plan, int32_t cap, float* ms, int32_t* kind);
+
+/* Release the plan and its CUDA graph (not the workspace). */
+void sfrd_destroy(sfrd_plan_t plan);
+
+/* Static description of an error code; text of the last CUDA error seen by
+ * this thread. */
+const char* sfrd_strerror(int code);
+const char* sfrd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFRD_H */

@@ -1,5 +1,5 @@
-"""Builds oracle problems from the shared workload descriptions (test side only)."""
-import oracle as O
+"""Builds oracle problems from the shared workload descriptions (oracle side; test infrastructure only)."""
+from . import sfrd_oracle as O
 
 
 def reaction_fns(cfg):

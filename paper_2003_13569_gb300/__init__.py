@@ -1,0 +1,253 @@
+"""Python binding of libsfrd.so, the sm_103a compact-MTT ETDRK4-P13 solver.
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  PyTorch supplies device memory (the workspace and the fields) and the
+CUDA stream; nothing here computes any part of the method.  If the shared
+library has not been built this module raises ImportError instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsfrd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libsfrd.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "(nvcc for sm_103a) before importing paper_2003_13569_gb300")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+SFRD_OK = 0
+ERRORS = {-1: "EINVAL", -2: "EUNSUPPORTED", -3: "ENOWS", -4: "ECUDA", -5: "ENONFINITE", -6: "ESTATE"}
+BC = {"periodic": 0, "dirichlet": 1, "neumann": 2}
+DTYPE = {"f64": 0, "f32": 1}
+REACTION = {"none": 0, "linear": 1, "fhn": 2, "gray_scott": 3, "schnakenberg": 4,
+            "gierer_meinhardt": 5, "huxley_mms": 6}
+COEFFICIENTS = ("R13", "Q13", "phi", "phi1", "phi2", "phi3")
+EXPORTS = ("sfrd_plan", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
+           "sfrd_store", "sfrd_run", "sfrd_step", "sfrd_run_host", "sfrd_forward", "sfrd_inverse",
+           "sfrd_coefficients", "sfrd_profile_step", "sfrd_destroy", "sfrd_strerror", "sfrd_last_error")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("N", ctypes.c_int64 * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3)]
+
+
+class Reaction(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nspecies", ctypes.c_int32), ("p", ctypes.c_double * 8),
+                ("offset", ctypes.c_double * 2)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("bc", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("nspecies", ctypes.c_int32), ("n", ctypes.c_int64 * 3), ("fft_len", ctypes.c_int64 * 3),
+                ("dof", ctypes.c_int64), ("kernels_per_step", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_lib.sfrd_plan.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(Grid), ctypes.c_int32, ctypes.POINTER(_D),
+                           ctypes.POINTER(_D), _D, ctypes.c_int32, ctypes.POINTER(Reaction)]
+_lib.sfrd_workspace_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+_lib.sfrd_get_info.argtypes = [_P, ctypes.POINTER(Info)]
+_lib.sfrd_bind.argtypes = [_P, _P, ctypes.c_size_t, _P]
+_lib.sfrd_load.argtypes = [_P, _P, _D]
+_lib.sfrd_advance.argtypes = [_P, ctypes.c_int64]
+_lib.sfrd_store.argtypes = [_P, _P]
+_lib.sfrd_run.argtypes = [_P, _P, _D, ctypes.c_int64]
+_lib.sfrd_step.argtypes = [_P, _P, _D]
+_lib.sfrd_run_host.argtypes = [_P, _P, _P, _D, ctypes.c_int64]
+_lib.sfrd_forward.argtypes = [_P, _P, _P]
+_lib.sfrd_inverse.argtypes = [_P, _P, _P]
+_lib.sfrd_coefficients.argtypes = [_P, ctypes.c_int32, _P]
+_lib.sfrd_profile_step.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(ctypes.c_int32)]
+_lib.sfrd_destroy.argtypes = [_P]
+_lib.sfrd_destroy.restype = None
+_lib.sfrd_strerror.argtypes = [ctypes.c_int]
+_lib.sfrd_strerror.restype = ctypes.c_char_p
+_lib.sfrd_last_error.argtypes = []
+_lib.sfrd_last_error.restype = ctypes.c_char_p
+for _name in EXPORTS:
+    if _name not in ("sfrd_destroy", "sfrd_strerror", "sfrd_last_error"):
+        getattr(_lib, _name).restype = ctypes.c_int
+
+
+class SfrdError(RuntimeError):
+    def __init__(self, code, where):
+        msg = "%s: %s (%s)" % (where, ERRORS.get(code, code), _lib.sfrd_strerror(code).decode())
+        if code == -4:
+            msg += ": " + _lib.sfrd_last_error().decode()
+        super().__init__(msg)
+        self.code = code
+
+
+def _check(code, where):
+    if code != SFRD_OK:
+        raise SfrdError(code, where)
+
+
+def lib():
+    """The loaded ctypes library (for tests of the raw C ABI)."""
+    return _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_plan(dim, N, lo, hi, bc, alpha, kappa, dt, dtype, reaction, params=(), offset=(0.0, 0.0),
+              nspecies=None):
+    """Create a raw plan handle (ctypes c_void_p); raises SfrdError on a negative code."""
+    g = Grid()
+    g.dim = dim
+    for d in range(3):
+        g.N[d] = int(N[d]) if d < dim else 1
+        g.lo[d] = float(lo[d]) if d < dim else 0.0
+        g.hi[d] = float(hi[d]) if d < dim else 1.0
+    r = Reaction()
+    r.kind = REACTION[reaction] if isinstance(reaction, str) else int(reaction)
+    S = nspecies if nspecies is not None else len(alpha)
+    r.nspecies = S
+    for i, v in enumerate(params):
+        r.p[i] = float(v)
+    r.offset[0], r.offset[1] = float(offset[0]), float(offset[1])
+    a = (ctypes.c_double * 2)(*[float(x) for x in alpha], *([0.0] * (2 - len(alpha))))
+    k = (ctypes.c_double * 2)(*[float(x) for x in kappa], *([0.0] * (2 - len(kappa))))
+    h = ctypes.c_void_p()
+    bcv = BC[bc] if isinstance(bc, str) else int(bc)
+    dtv = DTYPE[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(_lib.sfrd_plan(ctypes.byref(h), ctypes.byref(g), bcv, a, k, float(dt), dtv, ctypes.byref(r)),
+           "sfrd_plan")
+    return h
+
+
+class Solver:
+    """One plan bound to a torch-allocated workspace on the current CUDA device and stream."""
+
+    def __init__(self, cfg: dict, dtype: str | None = None, device=None):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.dtype = dtype or cfg["dtype"]
+        self.tdtype = torch.float32 if self.dtype == "f32" else torch.float64
+        r = cfg["reaction"]
+        self.S = len(cfg["alpha"])
+        self.handle = make_plan(cfg["dim"], cfg["N"], cfg["lo"], cfg["hi"], cfg["bc"], cfg["alpha"],
+                                cfg["kappa"], cfg["dt"], self.dtype, r["kind"], r.get("p", ()),
+                                r.get("offset", (0.0, 0.0)), nspecies=self.S)
+        info = Info()
+        _check(_lib.sfrd_get_info(self.handle, ctypes.byref(info)), "sfrd_get_info")
+        self.info = info
+        self.shape = tuple([self.S] + [int(info.n[d]) for d in reversed(range(cfg["dim"]))])
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.ws = torch.empty(int(info.workspace_bytes) + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = torch.cuda.current_stream(self.device)
+        _check(_lib.sfrd_bind(self.handle, ctypes.c_void_p(self._ws_ptr), int(info.workspace_bytes),
+                              ctypes.c_void_p(self.stream.cuda_stream)), "sfrd_bind")
+
+    # -- helpers -------------------------------------------------------------
+    def _field(self, u):
+        t = self.torch
+        if isinstance(u, np.ndarray) or isinstance(u, (list, tuple)):
+            u = t.as_tensor(np.stack([np.asarray(x) for x in u]) if isinstance(u, (list, tuple)) else u)
+        u = u.to(device=self.device, dtype=self.tdtype).contiguous()
+        if tuple(u.shape) != self.shape:
+            raise ValueError("field shape %s, expected %s" % (tuple(u.shape), self.shape))
+        return u
+
+    def empty(self):
+        return self.torch.empty(self.shape, dtype=self.tdtype, device=self.device)
+
+    @property
+    def dof(self):
+        return int(self.info.dof)
+
+    @property
+    def kernels_per_step(self):
+        return int(self.info.kernels_per_step)
+
+    # -- the C ABI -----------------------------------------------------------
+    def load(self, u0, t0=0.0):
+        u0 = self._field(u0)
+        self._keep = u0
+        _check(_lib.sfrd_load(self.handle, _ptr(u0), float(t0)), "sfrd_load")
+
+    def advance(self, nsteps):
+        _check(_lib.sfrd_advance(self.handle, int(nsteps)), "sfrd_advance")
+
+    def store(self, out=None):
+        out = self.empty() if out is None else out
+        _check(_lib.sfrd_store(self.handle, _ptr(out)), "sfrd_store")
+        return out
+
+    def run(self, u, t0=0.0, nsteps=1):
+        """Returns u(t0 + nsteps dt) as a new device tensor (the input is not modified)."""
+        w = self._field(u).clone()
+        _check(_lib.sfrd_run(self.handle, _ptr(w), float(t0), int(nsteps)), "sfrd_run")
+        return w
+
+    def step(self, u, t=0.0):
+        w = self._field(u).clone()
+        _check(_lib.sfrd_step(self.handle, _ptr(w), float(t)), "sfrd_step")
+        return w
+
+    def run_host(self, u_in: np.ndarray, t0=0.0, nsteps=1, out: np.ndarray | None = None):
+        """End-to-end through host memory (numpy arrays, ideally pinned); synchronises."""
+        npdt = np.float32 if self.dtype == "f32" else np.float64
+        if u_in.dtype != npdt or not u_in.flags.c_contiguous or tuple(u_in.shape) != self.shape:
+            raise ValueError("u_in must be a C-contiguous %s array of shape %s" % (npdt.__name__, self.shape))
+        out = np.empty_like(u_in) if out is None else out
+        _check(_lib.sfrd_run_host(self.handle, ctypes.c_void_p(u_in.ctypes.data), ctypes.c_void_p(out.ctypes.data),
+                                  float(t0), int(nsteps)), "sfrd_run_host")
+        return out
+
+    def run_host_ptr(self, src_ptr: int, dst_ptr: int, t0=0.0, nsteps=1):
+        _check(_lib.sfrd_run_host(self.handle, ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr), float(t0),
+                                  int(nsteps)), "sfrd_run_host")
+
+    def forward(self, u):
+        u = self._field(u)
+        out = self.empty()
+        _check(_lib.sfrd_forward(self.handle, _ptr(u), _ptr(out)), "sfrd_forward")
+        return out
+
+    def inverse(self, uhat):
+        uhat = self._field(uhat)
+        out = self.empty()
+        _check(_lib.sfrd_inverse(self.handle, _ptr(uhat), _ptr(out)), "sfrd_inverse")
+        return out
+
+    def coefficients(self, which):
+        w = COEFFICIENTS.index(which) if isinstance(which, str) else int(which)
+        out = self.empty()
+        _check(_lib.sfrd_coefficients(self.handle, w, _ptr(out)), "sfrd_coefficients")
+        return out
+
+    def profile_step(self):
+        """[(kind, ms)] for each kernel of one step (advances the resident state by one step)."""
+        n = self.kernels_per_step
+        ms = (ctypes.c_float * n)()
+        kd = (ctypes.c_int32 * n)()
+        _check(_lib.sfrd_profile_step(self.handle, n, ms, kd), "sfrd_profile_step")
+        return [(int(kd[i]), float(ms[i])) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.sfrd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,688 @@
+// Transform passes of one ETDRK4-P13 step and their launchers.
+//
+// Internal field layout (device workspace): species-major [S][n_z][n_y][pitch],
+// x contiguous, pitch = n_x rounded up to a multiple of 4 (padding held at 0).
+// Spectral arrays use the same layout with mode indices in eigenvalue order.
+//
+// One step (Algorithm 1, restructured by linearity so that each stage needs
+// one forward and one inverse separable transform per species) is four chains;
+// the slow axis is z in 3D and y in 2D:
+//   3D:  [middle y]  ->  [x: T_x, f, T_x]  ->  [middle y]  ->  [slow z: T_z, combine, T_z]
+//   2D:                  [x: T_x, f, T_x]  ->                  [slow y: T_y, combine, T_y]
+// The x pass carries the reaction (f at the stage time), the slow-axis pass
+// carries the Pade-(1,3) combination of Eq. ETDRK4P13:
+//   stage a:  a^ = Q13 u^ + phi F(f_u)
+//   stage b:  b^ = Q13 u^ + phi F(f_a)
+//   stage c:  c^ = Q13 (Q13 u^ + phi F(f_u)) + phi (2 F(f_b) - F(f_u))   [F(a) by linearity]
+//   update :  u^' = R13 u^ + phi1 F(f_u) + phi2 (F(f_a) + F(f_b)) + phi3 F(f_c)
+// where F = T_z T_y T_x is the unnormalised real transform of each axis and
+// the inverse is F / C.  All passes run in place on the work array.
+#pragma once
+
+#include "engine.cuh"
+
+namespace sfrd {
+
+// ---- reaction terms (Section 5.2; parameters as documented in sfrd.h) -----------
+
+template <typename T>
+__device__ __forceinline__ void react2(const ReactDev& re, T u, T v, T& fu, T& fv) {
+    switch (re.kind) {
+        case SFRD_REACT_FHN: {
+            const T mu = (T)re.p[0], eps = (T)re.p[1], beta = (T)re.p[2], gam = (T)re.p[3], del = (T)re.p[4];
+            fu = u * ((T)1 - u) * (u - mu) - v;
+            fv = eps * (beta * u - gam * v - del);
+        } break;
+        case SFRD_REACT_GRAY_SCOTT: {
+            const T F = (T)re.p[0], K = (T)re.p[1];
+            const T uvv = u * v * v;
+            fu = -uvv + F * ((T)1 - u);
+            fv = uvv - (F + K) * v;
+        } break;
+        case SFRD_REACT_SCHNAKENBERG: {
+            const T g = (T)re.p[0], a = (T)re.p[1], b = (T)re.p[2];
+            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
+            const T uuv = U * U * V;
+            fu = g * (a - U + uuv);
+            fv = g * (b - uuv);
+        } break;
+        case SFRD_REACT_GIERER_MEINHARDT: {
+            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
+            fu = (T)re.p[0] * U * U / V - (T)re.p[1] * U;
+            fv = (T)re.p[2] * U * U - (T)re.p[3] * V;
+        } break;
+        case SFRD_REACT_LINEAR:
+            fu = (T)re.p[0] * u;
+            fv = (T)re.p[0] * v;
+            break;
+        default:
+            fu = 0;
+            fv = 0;
+    }
+}
+
+// Single-species terms; x, y are node coordinates, t the stage time.
+template <typename T>
+__device__ __forceinline__ T react1(const ReactDev& re, T u, double x, double y, double t) {
+    switch (re.kind) {
+        case SFRD_REACT_LINEAR:
+            return (T)re.p[0] * u;
+        case SFRD_REACT_HUXLEY_MMS: {
+            // Example 2: exact solution t^alpha cos^3(2 pi x) cos^3(2 pi y); p = [alpha, k1..k4]
+            // with Phi = k1 c1x c1y + k2 c3x c1y + k3 c1x c3y + k4 c3x c3y, cNz = cos(2 N pi z).
+            const double al = re.p[0];
+            const double c1x = cospi(2.0 * x), c1y = cospi(2.0 * y);
+            const double c3x = cospi(6.0 * x), c3y = cospi(6.0 * y);
+            const double g = c1x * c1x * c1x * c1y * c1y * c1y;
+            const double Phi = re.p[1] * c1x * c1y + re.p[2] * c3x * c1y + re.p[3] * c1x * c3y + re.p[4] * c3x * c3y;
+            const double ta = t > 0 ? pow(t, al) : 0.0;
+            const double dta = t > 0 ? al * pow(t, al - 1.0) : 0.0;
+            const double w = ta * g;
+            const double src = dta * g + ta * Phi - w * (1.0 - w) * (w - 1.0);
+            return u * ((T)1 - u) * (u - (T)1) + (T)src;
+        }
+        default:
+            return 0;
+    }
+}
+
+// Value of the transform at unknown k from a DFT output held in slot order.
+template <typename C, bool PERM>
+__device__ __forceinline__ C get_one(const C* buf, int ldb, const AxisDev& ax, int k, int c) {
+    using T = decltype(buf[0].x);
+    C v;
+    if (ax.bc == SFRD_BC_PERIODIC) {
+        const int k1 = (ax.N - k) % ax.N;
+        const int r0 = PERM ? __ldg(ax.perm + k) : k;
+        const int r1 = PERM ? __ldg(ax.perm + k1) : k1;
+        const C z0 = buf[r0 * ldb + c], z1 = buf[r1 * ldb + c];
+        v.x = (T)0.5 * (z0.x + z1.x + z1.y - z0.y);
+        v.y = (T)0.5 * (z0.y + z1.y + z0.x - z1.x);
+        return v;
+    }
+    const int e = ext_index(ax.bc, k);
+    const int r0 = PERM ? __ldg(ax.perm + e) : e;
+    const C z = buf[r0 * ldb + c];
+    if (ax.bc == SFRD_BC_DIRICHLET) {
+        v.x = (T)-0.5 * z.y;
+        v.y = (T)0.5 * z.x;
+    } else {
+        v.x = (T)0.5 * z.x;
+        v.y = (T)0.5 * z.y;
+    }
+    return v;
+}
+
+// ---- strided-axis pass (y or z): tile = all unknowns along the axis x CC columns ----
+
+template <typename T, int CC, int MODE>
+__global__ void __launch_bounds__(kThreads) col_kernel(const ColArgs<T> a) {
+    using C = typename Cx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    constexpr int ldb = CC + 1;
+    constexpr int G = kThreads / CC;
+    const int tid = threadIdx.x, c = tid % CC, grp = tid / CC;
+    const AxisDev& ax = a.ax;
+    const int xA = blockIdx.x * a.xw + c;
+    const int xB = xA + a.bshift;
+    const long long other = blockIdx.y;
+
+    // load along the axis, natural order, with the odd/even extension
+    {
+        const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
+        const T* pA = a.in + other * a.in_sOther + xA;
+        for (int i = grp; i < ax.n; i += G) {
+            C z;
+            z.x = okA ? pA[i * a.in_sAxis] : (T)0;
+            z.y = okB ? pA[i * a.in_sAxis + a.in_offB] : (T)0;
+            put_extended<C, false>(buf, ldb, ax, i, c, z);
+        }
+        put_extension_zeros<C, false>(buf, ldb, ax, c, grp);
+    }
+    __syncthreads();
+    fft_dif(buf, ldb, ax, c, grp, G);
+
+    const int items = unpack_items(ax);
+    if (MODE == MODE_PLAIN) {
+        const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
+        T* qA = a.out + other * a.out_sOther + xA;
+        const T sc = (T)a.scale;
+        for (int it = grp; it < items; it += G) {
+            int k0, k1;
+            C v0, v1;
+            const int cnt = get_transform<C, true>(buf, ldb, ax, it, c, k0, v0, k1, v1);
+            if (okA) qA[k0 * a.out_sAxis] = v0.x * sc;
+            if (okB) qA[k0 * a.out_sAxis + a.out_offB] = v0.y * sc;
+            if (cnt == 2) {
+                if (okA) qA[k1 * a.out_sAxis] = v1.x * sc;
+                if (okB) qA[k1 * a.out_sAxis + a.out_offB] = v1.y * sc;
+            }
+        }
+        return;
+    }
+
+    // slow-axis modes: spectral combination, then the inverse along the axis
+    {
+        const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
+        const long long base = other * a.in_sOther + xA;
+        const long long oB = a.in_offB;
+        const T invC = (T)a.invC;
+        for (int it = grp; it < items; it += G) {
+            int ks[2];
+            C vs[2];
+            const int cnt = get_transform<C, true>(buf, ldb, ax, it, c, ks[0], vs[0], ks[1], vs[1]);
+            for (int q = 0; q < cnt; ++q) {
+                const int k = ks[q];
+                const long long iA = base + k * a.in_sAxis, iB = iA + oB;
+                T F[2] = {vs[q].x, vs[q].y};
+                T s[2] = {0, 0};
+                const bool ok[2] = {okA, okB};
+                const long long ix[2] = {iA, iB};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!ok[h]) continue;
+                    const long long i = ix[h];
+                    if (MODE == MODE_T0) {
+                        a.U[i] = F[h];
+                        s[h] = F[h];
+                    } else if (MODE == MODE_TA || MODE == MODE_TB) {
+                        if (MODE == MODE_TA) a.F1[i] = F[h]; else a.F2[i] = F[h];
+                        const T Q = a.CQ[2 * i], ph = a.CQ[2 * i + 1];
+                        s[h] = Q * a.U[i] + ph * F[h];
+                    } else if (MODE == MODE_TC) {
+                        a.F3[i] = F[h];
+                        const T Q = a.CQ[2 * i], ph = a.CQ[2 * i + 1];
+                        const T f1 = a.F1[i];
+                        const T ah = Q * a.U[i] + ph * f1;
+                        s[h] = Q * ah + ph * ((T)2 * F[h] - f1);
+                    } else {  // MODE_TD
+                        const T R = a.CR[4 * i], p1 = a.CR[4 * i + 1], p2 = a.CR[4 * i + 2], p3 = a.CR[4 * i + 3];
+                        const T un = R * a.U[i] + p1 * a.F1[i] + p2 * (a.F2[i] + a.F3[i]) + p3 * F[h];
+                        a.U[i] = un;
+                        s[h] = un;
+                    }
+                }
+                C z;
+                z.x = s[0] * invC;
+                z.y = s[1] * invC;
+                put_value<C, true>(buf, ldb, ax, k, c, z);
+            }
+        }
+        put_extension_zeros<C, true>(buf, ldb, ax, c, grp);
+    }
+    __syncthreads();
+    fft_dit(buf, ldb, ax, c, grp, G);
+    {
+        const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
+        T* qA = a.out + other * a.out_sOther + xA;
+        for (int i = grp; i < ax.n; i += G) {
+            const C v = get_one<C, false>(buf, ldb, ax, i, c);
+            if (okA) qA[i * a.out_sAxis] = v.x;
+            if (okB) qA[i * a.out_sAxis + a.out_offB] = v.y;
+        }
+    }
+    if (MODE == MODE_TD && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) a.clock->k += 1;
+}
+
+// ---- contiguous-axis pass: tile = CC row pairs (species 0 / species 1, or two rows) ----
+
+template <typename T, int CC, int MODE>
+__global__ void __launch_bounds__(kThreads) x_kernel(const XArgs<T> a) {
+    using C = typename Cx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    constexpr int ldb = CC + 1;
+    constexpr int G = kThreads / CC;
+    const int tid = threadIdx.x, c = tid % CC, grp = tid / CC;
+    const AxisDev& ax = a.ax;
+    const int n = ax.n;
+    const int shiftB = (a.S == 2) ? 0 : CC;
+    const int r0 = blockIdx.x * (a.S == 2 ? CC : 2 * CC);
+
+    // transposed load: consecutive threads read consecutive x of one row
+    for (int q = tid; q < CC * n; q += kThreads) {
+        const int cc = q / n, i = q - cc * n;
+        const int rA = r0 + cc, rB = rA + shiftB;
+        C z;
+        z.x = rA < a.rows ? a.in[(long long)rA * a.in_pitch + i] : (T)0;
+        z.y = rB < a.rows ? a.in[(long long)rA * a.in_pitch + a.in_offB + i] : (T)0;
+        put_extended<C, false>(buf, ldb, ax, i, cc, z);
+    }
+    if (tid < CC) put_extension_zeros<C, false>(buf, ldb, ax, tid, 0);
+    __syncthreads();
+    fft_dif(buf, ldb, ax, c, grp, G);
+
+    if (MODE == MODE_REACT) {
+        const double t = a.clock->t0 + ((double)a.clock->k + a.stage_frac) * a.tau;
+        const int items = unpack_items(ax);
+        const int rA = r0 + c, rB = rA + shiftB;
+        for (int it = grp; it < items; it += G) {
+            int ks[2];
+            C vs[2];
+            const int cnt = get_transform<C, true>(buf, ldb, ax, it, c, ks[0], vs[0], ks[1], vs[1]);
+            for (int q = 0; q < cnt; ++q) {
+                const int k = ks[q];
+                C f;
+                if (a.S == 2) {
+                    react2<T>(a.re, vs[q].x, vs[q].y, f.x, f.y);
+                } else {
+                    const double x = ax.lo + (ax.node0 + k) * ax.h;
+                    const int yA = rA % a.ny, yB = rB % a.ny;
+                    const double ya = a.ay.lo + (a.ay.node0 + yA) * a.ay.h;
+                    const double yb = a.ay.lo + (a.ay.node0 + yB) * a.ay.h;
+                    f.x = react1<T>(a.re, vs[q].x, x, ya, t);
+                    f.y = react1<T>(a.re, vs[q].y, x, yb, t);
+                }
+                put_value<C, true>(buf, ldb, ax, k, c, f);
+            }
+        }
+        put_extension_zeros<C, true>(buf, ldb, ax, c, grp);
+        __syncthreads();
+        fft_dit(buf, ldb, ax, c, grp, G);
+        for (int q = tid; q < CC * n; q += kThreads) {
+            const int cc = q / n, i = q - cc * n;
+            const int rA2 = r0 + cc, rB2 = rA2 + shiftB;
+            const C v = get_one<C, false>(buf, ldb, ax, i, cc);
+            if (rA2 < a.rows) a.out[(long long)rA2 * a.out_pitch + i] = v.x;
+            if (rB2 < a.rows) a.out[(long long)rA2 * a.out_pitch + a.out_offB + i] = v.y;
+        }
+    } else {
+        for (int q = tid; q < CC * n; q += kThreads) {
+            const int cc = q / n, i = q - cc * n;
+            const int rA2 = r0 + cc, rB2 = rA2 + shiftB;
+            const C v = get_one<C, true>(buf, ldb, ax, i, cc);
+            if (rA2 < a.rows) a.out[(long long)rA2 * a.out_pitch + i] = v.x;
+            if (rB2 < a.rows) a.out[(long long)rA2 * a.out_pitch + a.out_offB + i] = v.y;
+        }
+    }
+    // keep the padding columns of internal rows at zero
+    const int pad = a.out_fill - n;
+    if (pad > 0) {
+        for (int q = tid; q < CC * pad; q += kThreads) {
+            const int cc = q / pad, i = n + (q - cc * pad);
+            const int rA2 = r0 + cc, rB2 = rA2 + shiftB;
+            if (rA2 < a.rows) a.out[(long long)rA2 * a.out_pitch + i] = (T)0;
+            if (rB2 < a.rows) a.out[(long long)rA2 * a.out_pitch + a.out_offB + i] = (T)0;
+        }
+    }
+}
+
+// ---- plan-time FP64 coefficient kernel (Algorithm 1, precompute lines) ----------
+
+template <typename T>
+__global__ void coef_init_kernel(const double* __restrict__ lx, const double* __restrict__ ly,
+                                 const double* __restrict__ lz, int nx, int ny, int nz, int pitch,
+                                 int S, double a0, double a1, double k0, double k1, double tau,
+                                 T* __restrict__ CQ, T* __restrict__ CR) {
+    const long long total = (long long)S * nz * ny * pitch;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % pitch);
+        long long r = idx / pitch;
+        const int y = (int)(r % ny);
+        r /= ny;
+        const int z = (int)(r % nz);
+        const int s = (int)(r / nz);
+        double Q = 0, ph = 0, R = 0, p1 = 0, p2 = 0, p3 = 0;
+        if (x < nx) {
+            const double Lam = lx[x] + ly[y] + lz[z];           // summed eigenvalue (Eqs. E16-E22)
+            const double alpha = s == 0 ? a0 : a1, kappa = s == 0 ? k0 : k1;
+            const double Lf = Lam > 0.0 ? pow(Lam, 0.5 * alpha) : 0.0;   // Lambda^{alpha/2}
+            const double L = kappa * tau * Lf;                  // L = kappa tau Lambda^{alpha/2}
+            const double D1 = 24.0 + L * (18.0 + L * (6.0 + L));
+            const double D2 = 192.0 + L * (72.0 + L * (12.0 + L));
+            R = (24.0 - 6.0 * L) / D1;
+            Q = 24.0 * (8.0 - L) / D2;
+            ph = tau * (96.0 + L * (12.0 + L)) / D2;
+            p1 = tau * (4.0 - L) / D1;
+            p2 = 2.0 * tau * (4.0 + L) / D1;
+            p3 = tau * (4.0 + L * (3.0 + L)) / D1;
+        }
+        CQ[2 * idx] = (T)Q;
+        CQ[2 * idx + 1] = (T)ph;
+        CR[4 * idx] = (T)R;
+        CR[4 * idx + 1] = (T)p1;
+        CR[4 * idx + 2] = (T)p2;
+        CR[4 * idx + 3] = (T)p3;
+    }
+}
+
+// which: 0 R13, 1 Q13, 2 phi, 3 phi1, 4 phi2, 5 phi3 -> dense [S][nz][ny][nx]
+template <typename T>
+__global__ void coef_copy_kernel(const T* __restrict__ CQ, const T* __restrict__ CR, int which, int nx,
+                                 int ny, int nz, int pitch, int S, T* __restrict__ out) {
+    const long long total = (long long)S * nz * ny * nx;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % nx);
+        const long long row = idx / nx;
+        const long long j = row * pitch + x;
+        T v;
+        switch (which) {
+            case 0: v = CR[4 * j]; break;
+            case 1: v = CQ[2 * j]; break;
+            case 2: v = CQ[2 * j + 1]; break;
+            case 3: v = CR[4 * j + 1]; break;
+            case 4: v = CR[4 * j + 2]; break;
+            default: v = CR[4 * j + 3]; break;
+        }
+        out[idx] = v;
+    }
+}
+
+// ---- launchers -------------------------------------------------------------------
+
+#define SFRD_TRY(x)                          \
+    do {                                     \
+        cudaError_t e_ = (x);                \
+        if (e_ != cudaSuccess) return e_;    \
+    } while (0)
+
+template <typename T, int CC>
+static cudaError_t col_launch(const ColArgs<T>& a, int mode, dim3 grid, size_t smem, cudaStream_t s) {
+    void (*k)(const ColArgs<T>) = nullptr;
+    switch (mode) {
+        case MODE_PLAIN: k = col_kernel<T, CC, MODE_PLAIN>; break;
+        case MODE_T0: k = col_kernel<T, CC, MODE_T0>; break;
+        case MODE_TA: k = col_kernel<T, CC, MODE_TA>; break;
+        case MODE_TB: k = col_kernel<T, CC, MODE_TB>; break;
+        case MODE_TC: k = col_kernel<T, CC, MODE_TC>; break;
+        default: k = col_kernel<T, CC, MODE_TD>; break;
+    }
+    k<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int CC>
+static cudaError_t x_launch(const XArgs<T>& a, int mode, dim3 grid, size_t smem, cudaStream_t s) {
+    void (*k)(const XArgs<T>) = (mode == MODE_REACT) ? x_kernel<T, CC, MODE_REACT> : x_kernel<T, CC, MODE_PLAIN>;
+    k<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Raise the dynamic shared-memory limit of every pass kernel of one tile width
+// (done once at bind time, outside any stream capture).
+constexpr int kMaxDynSmem = 227 * 1024;
+
+template <typename T, int CC>
+static cudaError_t prepare_cc() {
+    void (*ks[])(const ColArgs<T>) = {col_kernel<T, CC, MODE_PLAIN>, col_kernel<T, CC, MODE_T0>,
+                                      col_kernel<T, CC, MODE_TA>,    col_kernel<T, CC, MODE_TB>,
+                                      col_kernel<T, CC, MODE_TC>,    col_kernel<T, CC, MODE_TD>};
+    for (auto k : ks) SFRD_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+    void (*xs[])(const XArgs<T>) = {x_kernel<T, CC, MODE_PLAIN>, x_kernel<T, CC, MODE_REACT>};
+    for (auto k : xs) SFRD_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+    return cudaSuccess;
+}
+
+template <typename T> struct CCs;
+template <> struct CCs<float> { static constexpr int a = 16, b = 8, c = 4; };
+template <> struct CCs<double> { static constexpr int a = 8, b = 4, c = 2; };
+
+template <typename T>
+static AxisDev axis_dev(const Plan& p, int d) {
+    AxisDev ax{};
+    ax.n = p.n[d];
+    ax.N = (int)p.Nint[d];
+    ax.M = p.M[d];
+    ax.bc = p.bc;
+    ax.nst = (int)p.radix[d].size();
+    for (int i = 0; i < ax.nst; ++i) ax.radix[i] = p.radix[d][i];
+    ax.tw = p.ws + p.off_tw[d];
+    ax.perm = reinterpret_cast<const int*>(p.ws + p.off_perm[d]);
+    ax.node0 = p.bc == SFRD_BC_DIRICHLET ? 1 : 0;
+    ax.h = (p.hi[d] - p.lo[d]) / (double)p.Nint[d];
+    ax.lo = p.lo[d];
+    return ax;
+}
+
+template <typename T>
+static size_t tile_smem(const Plan& p, int d) {
+    return (size_t)p.M[d] * (size_t)(p.CC + 1) * 2 * sizeof(T);
+}
+
+template <typename T>
+static cudaError_t dispatch_col(const Plan& p, const ColArgs<T>& a, int mode, dim3 grid, size_t smem, cudaStream_t s) {
+    if (p.CC == CCs<T>::a) return col_launch<T, CCs<T>::a>(a, mode, grid, smem, s);
+    if (p.CC == CCs<T>::b) return col_launch<T, CCs<T>::b>(a, mode, grid, smem, s);
+    return col_launch<T, CCs<T>::c>(a, mode, grid, smem, s);
+}
+
+template <typename T>
+static cudaError_t dispatch_x(const Plan& p, const XArgs<T>& a, int mode, dim3 grid, size_t smem, cudaStream_t s) {
+    if (p.CC == CCs<T>::a) return x_launch<T, CCs<T>::a>(a, mode, grid, smem, s);
+    if (p.CC == CCs<T>::b) return x_launch<T, CCs<T>::b>(a, mode, grid, smem, s);
+    return x_launch<T, CCs<T>::c>(a, mode, grid, smem, s);
+}
+
+template <typename T>
+cudaError_t prepare_kernels(const Plan& p) {
+    (void)p;
+    SFRD_TRY((prepare_cc<T, CCs<T>::a>()));
+    SFRD_TRY((prepare_cc<T, CCs<T>::b>()));
+    return prepare_cc<T, CCs<T>::c>();
+}
+
+template <typename T> static T* wsT(const Plan& p, size_t off) { return reinterpret_cast<T*>(p.ws + off); }
+
+// Array description: base pointer, row pitch, species plane stride.
+template <typename T>
+struct Arr {
+    const T* ptr;
+    long long pitch;
+    long long plane;
+    int xlim;
+};
+
+template <typename T>
+static Arr<T> internal_arr(const Plan& p, size_t off) {
+    return Arr<T>{wsT<T>(p, off), p.pitch, p.plane, p.pitch};
+}
+
+template <typename T>
+static Arr<T> dense_arr(const Plan& p, const void* ptr) {
+    return Arr<T>{static_cast<const T*>(ptr), p.n[0], p.dense, p.n[0]};
+}
+
+// Strided pass along axis d (1 = y, 2 = z) from array `in` to `out`.
+template <typename T>
+static cudaError_t run_col(const Plan& p, int d, int mode, const Arr<T>& in, const Arr<T>& out, double scale,
+                           cudaStream_t s) {
+    ColArgs<T> a{};
+    const int ny = p.n[1];
+    a.in = in.ptr;
+    a.out = const_cast<T*>(out.ptr);
+    const bool two = p.S == 2;
+    a.bshift = two ? 0 : p.CC;
+    a.xw = two ? p.CC : 2 * p.CC;
+    a.in_offB = two ? in.plane : p.CC;
+    a.out_offB = two ? out.plane : p.CC;
+    int gy = 1;
+    if (d == 2) {          // z in 3D: blockIdx.y = y
+        a.in_sAxis = (long long)ny * in.pitch;
+        a.in_sOther = in.pitch;
+        a.out_sAxis = (long long)ny * out.pitch;
+        a.out_sOther = out.pitch;
+        gy = ny;
+    } else if (p.dim == 3) {   // y in 3D: blockIdx.y = z
+        a.in_sAxis = in.pitch;
+        a.in_sOther = (long long)ny * in.pitch;
+        a.out_sAxis = out.pitch;
+        a.out_sOther = (long long)ny * out.pitch;
+        gy = p.n[2];
+    } else {               // y in 2D
+        a.in_sAxis = in.pitch;
+        a.in_sOther = 0;
+        a.out_sAxis = out.pitch;
+        a.out_sOther = 0;
+        gy = 1;
+    }
+    a.in_xlim = in.xlim;
+    a.out_xlim = out.xlim;
+    a.scale = scale;
+    double C = 1.0;
+    for (int k = 0; k < p.dim; ++k) C *= (p.bc == SFRD_BC_PERIODIC) ? (double)p.Nint[k] : 0.5 * (double)p.Nint[k];
+    a.invC = 1.0 / C;
+    a.U = wsT<T>(p, p.off_U);
+    a.F1 = wsT<T>(p, p.off_F1);
+    a.F2 = wsT<T>(p, p.off_F2);
+    a.F3 = wsT<T>(p, p.off_F3);
+    a.CQ = wsT<T>(p, p.off_CQ);
+    a.CR = wsT<T>(p, p.off_CR);
+    a.clock = reinterpret_cast<Clock*>(p.ws + p.off_clock);
+    a.ax = axis_dev<T>(p, d);
+    const int xlim = in.xlim > out.xlim ? in.xlim : out.xlim;
+    dim3 grid((xlim + a.xw - 1) / a.xw, gy, 1);
+    return dispatch_col<T>(p, a, mode, grid, tile_smem<T>(p, d), s);
+}
+
+template <typename T>
+static cudaError_t run_x(const Plan& p, int mode, const Arr<T>& in, const Arr<T>& out, int out_fill,
+                         double stage_frac, cudaStream_t s) {
+    XArgs<T> a{};
+    a.in = in.ptr;
+    a.out = const_cast<T*>(out.ptr);
+    const bool two = p.S == 2;
+    a.S = p.S;
+    a.in_pitch = in.pitch;
+    a.out_pitch = out.pitch;
+    a.in_offB = two ? in.plane : (long long)p.CC * in.pitch;
+    a.out_offB = two ? out.plane : (long long)p.CC * out.pitch;
+    a.rows = p.n[1] * p.n[2];
+    a.out_fill = out_fill;
+    a.ny = p.n[1];
+    a.tau = p.dt;
+    a.stage_frac = stage_frac;
+    a.clock = reinterpret_cast<const Clock*>(p.ws + p.off_clock);
+    a.ax = axis_dev<T>(p, 0);
+    a.ay = axis_dev<T>(p, 1);
+    if (p.dim == 3) a.az = axis_dev<T>(p, 2);
+    a.re = p.re;
+    const int per = two ? p.CC : 2 * p.CC;
+    dim3 grid((a.rows + per - 1) / per, 1, 1);
+    return dispatch_x<T>(p, a, mode, grid, tile_smem<T>(p, 0), s);
+}
+
+// One step.  With `ev` non-null, event ev[i] is recorded before launch i and
+// ev[i+1] after it, and kind[i] receives the pass kind (PassKind).
+template <typename T>
+static cudaError_t step_impl(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind, int cap) {
+    const Arr<T> W = internal_arr<T>(p, p.off_W);
+    const int slow = p.dim == 3 ? 2 : 1;
+    static const double frac[4] = {0.0, 0.5, 0.5, 1.0};
+    int i = 0;
+    auto mark = [&](int k) -> cudaError_t {
+        if (!ev || i >= cap) return cudaSuccess;
+        if (kind) kind[i] = k;
+        return cudaEventRecord(ev[i], s);
+    };
+    auto done = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (ev && i < cap) e = cudaEventRecord(ev[i + 1], s);
+        ++i;
+        return e;
+    };
+    for (int st = 0; st < 4; ++st) {
+        if (p.dim == 3) {
+            SFRD_TRY(mark(PASS_MID));
+            SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W, W, 1.0, s));
+            SFRD_TRY(done());
+        }
+        SFRD_TRY(mark(PASS_X));
+        SFRD_TRY(run_x<T>(p, MODE_REACT, W, W, p.pitch, frac[st], s));
+        SFRD_TRY(done());
+        if (p.dim == 3) {
+            SFRD_TRY(mark(PASS_MID));
+            SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W, W, 1.0, s));
+            SFRD_TRY(done());
+        }
+        SFRD_TRY(mark(PASS_SLOW_A + st));
+        SFRD_TRY(run_col<T>(p, slow, MODE_TA + st, W, W, 1.0, s));
+        SFRD_TRY(done());
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_step(Plan& p, cudaStream_t s) {
+    return step_impl<T>(p, s, nullptr, nullptr, 0);
+}
+
+template <typename T>
+cudaError_t launch_step_profiled(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind, int cap) {
+    return step_impl<T>(p, s, ev, kind, cap);
+}
+
+template <typename T>
+cudaError_t launch_load(Plan& p, const void* u0, cudaStream_t s) {
+    const Arr<T> W = internal_arr<T>(p, p.off_W);
+    const int slow = p.dim == 3 ? 2 : 1;
+    SFRD_TRY(run_x<T>(p, MODE_PLAIN, dense_arr<T>(p, u0), W, p.pitch, 0.0, s));
+    if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W, W, 1.0, s));
+    return run_col<T>(p, slow, MODE_T0, W, W, 1.0, s);
+}
+
+template <typename T>
+cudaError_t launch_store(Plan& p, void* u, cudaStream_t s) {
+    const Arr<T> W = internal_arr<T>(p, p.off_W);
+    const Arr<T> W2 = internal_arr<T>(p, p.off_W2);
+    if (p.dim == 3) {
+        SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W, W2, 1.0, s));
+        return run_x<T>(p, MODE_PLAIN, W2, dense_arr<T>(p, u), 0, 0.0, s);
+    }
+    return run_x<T>(p, MODE_PLAIN, W, dense_arr<T>(p, u), 0, 0.0, s);
+}
+
+template <typename T>
+cudaError_t launch_forward(Plan& p, const void* u, void* uhat, cudaStream_t s) {
+    const Arr<T> W2 = internal_arr<T>(p, p.off_W2);
+    const int slow = p.dim == 3 ? 2 : 1;
+    SFRD_TRY(run_x<T>(p, MODE_PLAIN, dense_arr<T>(p, u), W2, p.pitch, 0.0, s));
+    if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
+    return run_col<T>(p, slow, MODE_PLAIN, W2, dense_arr<T>(p, uhat), 1.0, s);
+}
+
+template <typename T>
+cudaError_t launch_inverse(Plan& p, const void* uhat, void* u, cudaStream_t s) {
+    const Arr<T> W2 = internal_arr<T>(p, p.off_W2);
+    const int slow = p.dim == 3 ? 2 : 1;
+    double C = 1.0;
+    for (int k = 0; k < p.dim; ++k) C *= (p.bc == SFRD_BC_PERIODIC) ? (double)p.Nint[k] : 0.5 * (double)p.Nint[k];
+    SFRD_TRY(cudaMemsetAsync(p.ws + p.off_W2, 0, (size_t)p.S * p.plane * sizeof(T), s));
+    SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, dense_arr<T>(p, uhat), W2, 1.0 / C, s));
+    if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
+    return run_x<T>(p, MODE_PLAIN, W2, dense_arr<T>(p, u), 0, 0.0, s);
+}
+
+template <typename T>
+cudaError_t launch_coef_init(Plan& p, cudaStream_t s) {
+    const double* lx = reinterpret_cast<const double*>(p.ws + p.off_lam[0]);
+    const double* ly = reinterpret_cast<const double*>(p.ws + p.off_lam[1]);
+    const double* lz = reinterpret_cast<const double*>(p.ws + p.off_lam[2]);
+    const double a1 = p.S == 2 ? p.alpha[1] : p.alpha[0];
+    const double k1 = p.S == 2 ? p.kappa[1] : p.kappa[0];
+    coef_init_kernel<T><<<1024, 256, 0, s>>>(lx, ly, lz, p.n[0], p.n[1], p.n[2], p.pitch, p.S, p.alpha[0], a1,
+                                             p.kappa[0], k1, p.dt, wsT<T>(p, p.off_CQ), wsT<T>(p, p.off_CR));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coef_copy(Plan& p, int which, void* out, cudaStream_t s) {
+    coef_copy_kernel<T><<<1024, 256, 0, s>>>(wsT<T>(p, p.off_CQ), wsT<T>(p, p.off_CR), which, p.n[0], p.n[1], p.n[2],
+                                             p.pitch, p.S, static_cast<T*>(out));
+    return cudaGetLastError();
+}
+
+#define SFRD_INSTANTIATE(T)                                                                  \
+    template cudaError_t launch_step<T>(Plan&, cudaStream_t);                                \
+    template cudaError_t launch_step_profiled<T>(Plan&, cudaStream_t, cudaEvent_t*, int*, int); \
+    template cudaError_t launch_load<T>(Plan&, const void*, cudaStream_t);                   \
+    template cudaError_t launch_store<T>(Plan&, void*, cudaStream_t);                        \
+    template cudaError_t launch_forward<T>(Plan&, const void*, void*, cudaStream_t);         \
+    template cudaError_t launch_inverse<T>(Plan&, const void*, void*, cudaStream_t);         \
+    template cudaError_t launch_coef_init<T>(Plan&, cudaStream_t);                           \
+    template cudaError_t launch_coef_copy<T>(Plan&, int, void*, cudaStream_t);          \
+    template cudaError_t prepare_kernels<T>(const Plan&);
+
+}  // namespace sfrd

@@ -1,0 +1,533 @@
+// C ABI: plan construction (validation, FP64 tables, workspace layout), binding,
+// and the load / advance / store sequencing with a captured CUDA graph per step.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sfrd_internal.h"
+
+namespace sfrd {
+
+static thread_local std::string g_last_error;
+
+static int cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return SFRD_ECUDA;
+}
+
+#define SFRD_CUDA(call)                                      \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+__global__ void set_clock_kernel(Clock* c, double t0) {
+    c->t0 = t0;
+    c->k = 0;
+}
+
+cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s) {
+    set_clock_kernel<<<1, 1, 0, s>>>(reinterpret_cast<Clock*>(p.ws + p.off_clock), t0);
+    return cudaGetLastError();
+}
+
+int kernels_per_step(const Plan& p) { return p.dim == 3 ? 16 : 8; }
+
+// cos and sin of 2 pi k / M with exact octant reduction in long double.
+static void cos_sin_2pi(long long k, long long M, double& c, double& s) {
+    long long r = k % M;
+    if (r < 0) r += M;
+    const long long q = (4 * r) / M;          // quadrant
+    const long long rem = 4 * r - q * M;       // angle within quadrant = (pi/2) rem / M
+    long double c0, s0;
+    const long double half_pi = 1.57079632679489661923132169163975144L;
+    if (2 * rem <= M) {
+        const long double th = half_pi * (long double)rem / (long double)M;
+        c0 = cosl(th);
+        s0 = sinl(th);
+    } else {
+        const long double th = half_pi * (long double)(M - rem) / (long double)M;
+        c0 = sinl(th);
+        s0 = cosl(th);
+    }
+    long double cc, ss;
+    switch (q) {
+        case 0: cc = c0; ss = s0; break;
+        case 1: cc = -s0; ss = c0; break;
+        case 2: cc = -c0; ss = -s0; break;
+        default: cc = s0; ss = -c0; break;
+    }
+    c = (double)cc;
+    s = (double)ss;
+}
+
+// Mixed-radix factorisation: 8s, a 4 (or 4*4 in place of 8*2), then 3s and 5s.
+static bool factor(int M, std::vector<int>& r) {
+    r.clear();
+    int m = M, k2 = 0;
+    while (m % 2 == 0) { m /= 2; ++k2; }
+    int n8 = k2 / 3, rem = k2 % 3;
+    if (rem == 1 && n8 > 0) { --n8; r.push_back(4); r.push_back(4); }
+    for (int i = 0; i < n8; ++i) r.push_back(8);
+    if (rem == 2) r.push_back(4);
+    if (rem == 1 && k2 == 1) r.push_back(2);
+    while (m % 3 == 0) { m /= 3; r.push_back(3); }
+    while (m % 5 == 0) { m /= 5; r.push_back(5); }
+    return m == 1 && (int)r.size() <= kMaxStages;
+}
+
+// Slot of extension index k after the in-place DIF with radices r[0..s-1]:
+// slot = sum_t d_t * M / (r_0 ... r_t), d_t the mixed-radix digits of k (least
+// significant first, base r_0, r_1, ...).
+static void dif_perm(int M, const std::vector<int>& r, std::vector<int>& perm) {
+    perm.assign(M, 0);
+    for (int k = 0; k < M; ++k) {
+        int kk = k, pos = 0, w = M;
+        for (int R : r) {
+            const int d = kk % R;
+            kk /= R;
+            w /= R;
+            pos += d * w;
+        }
+        perm[k] = pos;
+    }
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int unknowns(int bc, long long N) {
+    return bc == SFRD_BC_PERIODIC ? (int)N : (bc == SFRD_BC_DIRICHLET ? (int)N - 1 : (int)N + 1);
+}
+
+static int create(Plan** out, const sfrd_grid* g, int bc, const double* alpha, const double* kappa, double dt,
+                  int dtype, const sfrd_reaction* re) {
+    if (!out || !g || !alpha || !kappa || !re) return SFRD_EINVAL;
+    *out = nullptr;
+    if (bc < 0 || bc > 2 || (dtype != SFRD_F32 && dtype != SFRD_F64)) return SFRD_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return SFRD_EINVAL;
+    if (g->dim < 1 || g->dim > 3) return SFRD_EINVAL;
+    if (re->nspecies < 1 || re->nspecies > 2) return SFRD_EINVAL;
+    const int S = re->nspecies;
+    for (int s = 0; s < S; ++s) {
+        if (!(alpha[s] > 1.0 && alpha[s] <= 2.0)) return SFRD_EINVAL;   // Eq. 1: 1 < alpha <= 2
+        if (!(kappa[s] >= 0.0) || !std::isfinite(kappa[s])) return SFRD_EINVAL;
+    }
+    for (int d = 0; d < g->dim; ++d) {
+        if (g->N[d] < 2) return SFRD_EINVAL;
+        if (!(g->hi[d] > g->lo[d]) || !std::isfinite(g->hi[d] - g->lo[d])) return SFRD_EINVAL;
+    }
+    switch (re->kind) {
+        case SFRD_REACT_NONE:
+        case SFRD_REACT_LINEAR:
+            break;
+        case SFRD_REACT_FHN:
+        case SFRD_REACT_GRAY_SCOTT:
+        case SFRD_REACT_SCHNAKENBERG:
+        case SFRD_REACT_GIERER_MEINHARDT:
+            if (S != 2) return SFRD_EINVAL;
+            break;
+        case SFRD_REACT_HUXLEY_MMS:
+            if (S != 1 || g->dim != 2) return SFRD_EINVAL;
+            break;
+        default:
+            return SFRD_EINVAL;
+    }
+    if (g->dim == 1) return SFRD_EUNSUPPORTED;
+
+    Plan* p = new (std::nothrow) Plan();
+    if (!p) return SFRD_EINVAL;
+    p->dim = g->dim;
+    p->bc = bc;
+    p->dtype = dtype;
+    p->S = S;
+    p->esize = dtype == SFRD_F32 ? 4 : 8;
+    p->dt = dt;
+    for (int s = 0; s < S; ++s) {
+        p->alpha[s] = alpha[s];
+        p->kappa[s] = kappa[s];
+    }
+    for (int d = 0; d < 3; ++d) {
+        if (d < g->dim) {
+            p->Nint[d] = g->N[d];
+            p->lo[d] = g->lo[d];
+            p->hi[d] = g->hi[d];
+            p->n[d] = unknowns(bc, g->N[d]);
+            const long long M = bc == SFRD_BC_PERIODIC ? g->N[d] : 2 * g->N[d];
+            if (M > kMaxFFT || !factor((int)M, p->radix[d])) {
+                delete p;
+                return SFRD_EUNSUPPORTED;
+            }
+            p->M[d] = (int)M;
+        } else {
+            p->Nint[d] = 1;
+            p->n[d] = 1;
+            p->M[d] = 1;
+        }
+    }
+    p->pitch = (p->n[0] + 3) / 4 * 4;
+    p->plane = (long long)p->n[2] * p->n[1] * p->pitch;
+    p->dense = (long long)p->n[2] * p->n[1] * p->n[0];
+
+    // reaction parameters (host-side constants of the manufactured source)
+    p->re.kind = re->kind;
+    p->re.S = S;
+    for (int i = 0; i < 8; ++i) p->re.p[i] = re->p[i];
+    p->re.off[0] = re->offset[0];
+    p->re.off[1] = re->offset[1];
+    if (re->kind == SFRD_REACT_HUXLEY_MMS) {
+        const double a = alpha[0], k = kappa[0], pi2 = M_PI * M_PI;
+        p->re.p[0] = a;
+        p->re.p[1] = k / 16.0 * 9.0 * std::pow(8.0 * pi2, a / 2);
+        p->re.p[2] = k / 16.0 * 3.0 * std::pow(40.0 * pi2, a / 2);
+        p->re.p[3] = k / 16.0 * 3.0 * std::pow(40.0 * pi2, a / 2);
+        p->re.p[4] = k / 16.0 * std::pow(72.0 * pi2, a / 2);
+    }
+
+    // FP64 tables: eigenvalues (Section 3.1), twiddles omega_M^k, DIF slot permutation
+    for (int d = 0; d < 3; ++d) {
+        if (d >= g->dim) {
+            p->lam[d].assign(1, 0.0);
+            continue;
+        }
+        const long long N = p->Nint[d];
+        const double h = (p->hi[d] - p->lo[d]) / (double)N;
+        p->lam[d].resize(p->n[d]);
+        for (int i = 0; i < p->n[d]; ++i) {
+            double c, s;
+            if (bc == SFRD_BC_PERIODIC) cos_sin_2pi(i, 2 * N, c, s);                    // sin(pi k / N)
+            else cos_sin_2pi(i + (bc == SFRD_BC_DIRICHLET ? 1 : 0), 4 * N, c, s);      // sin(n pi / (2N))
+            const double s2 = s * s;
+            p->lam[d][i] = 4.0 * s2 / (h * h * (1.0 - s2 / 3.0));
+        }
+        const int M = p->M[d];
+        p->tw64[d].resize(2 * M);
+        p->tw32[d].resize(2 * M);
+        for (int k = 0; k < M; ++k) {
+            double c, s;
+            cos_sin_2pi(k, M, c, s);
+            p->tw64[d][2 * k] = c;
+            p->tw64[d][2 * k + 1] = -s;
+            p->tw32[d][2 * k] = (float)c;
+            p->tw32[d][2 * k + 1] = (float)-s;
+        }
+        dif_perm(M, p->radix[d], p->perm[d]);
+    }
+
+    // tile width: the widest tile that still gives >= 2 blocks per SM on the smallest pass
+    const int cands32[3] = {16, 8, 4}, cands64[3] = {8, 4, 2};
+    const int* cands = dtype == SFRD_F32 ? cands32 : cands64;
+    p->CC = cands[2];
+    for (int i = 0; i < 3; ++i) {
+        const int cc = cands[i];
+        const int xw = S == 2 ? cc : 2 * cc;
+        const long long rows = (long long)p->n[1] * p->n[2];
+        const long long xblocks = (rows + xw - 1) / xw;
+        const long long sblocks = (long long)((p->pitch + xw - 1) / xw) * (p->dim == 3 ? p->n[1] : 1);
+        if (xblocks >= 304 && sblocks >= 304) {
+            p->CC = cc;
+            break;
+        }
+    }
+
+    // workspace layout
+    const size_t E = p->esize, fld = (size_t)S * p->plane * E;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+    p->off_W = take(fld);
+    p->off_W2 = take(fld);
+    p->off_U = take(fld);
+    p->off_F1 = take(fld);
+    p->off_F2 = take(fld);
+    p->off_F3 = take(fld);
+    p->off_CQ = take(2 * fld);
+    p->off_CR = take(4 * fld);
+    p->off_D = take((size_t)S * p->dense * E);
+    p->off_clock = take(sizeof(Clock));
+    for (int d = 0; d < 3; ++d) {
+        p->off_tw[d] = take((size_t)p->M[d] * 2 * E);
+        p->off_perm[d] = take((size_t)p->M[d] * sizeof(int));
+        p->off_lam[d] = take(p->lam[d].size() * sizeof(double));
+    }
+    p->ws_bytes = o;
+    *out = p;
+    return SFRD_OK;
+}
+
+static void drop_graph(Plan* p) {
+    if (p->step_exec) cudaGraphExecDestroy(p->step_exec);
+    if (p->step_graph) cudaGraphDestroy(p->step_graph);
+    p->step_exec = nullptr;
+    p->step_graph = nullptr;
+}
+
+static int bind(Plan* p, void* ws, size_t bytes, void* stream) {
+    if (!ws || bytes < p->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255u)) return SFRD_ENOWS;
+    drop_graph(p);
+    p->ws = static_cast<char*>(ws);
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->loaded = false;
+    if (!p->cap_stream) SFRD_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t s = p->stream;
+    const size_t E = p->esize;
+    for (int d = 0; d < 3; ++d) {
+        const void* tw = p->dtype == SFRD_F32 ? (const void*)p->tw32[d].data() : (const void*)p->tw64[d].data();
+        SFRD_CUDA(cudaMemcpyAsync(p->ws + p->off_tw[d], tw, (size_t)p->M[d] * 2 * E, cudaMemcpyHostToDevice, s));
+        SFRD_CUDA(cudaMemcpyAsync(p->ws + p->off_perm[d], p->perm[d].data(), (size_t)p->M[d] * sizeof(int),
+                                  cudaMemcpyHostToDevice, s));
+        SFRD_CUDA(cudaMemcpyAsync(p->ws + p->off_lam[d], p->lam[d].data(), p->lam[d].size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, s));
+    }
+    const size_t fld = (size_t)p->S * p->plane * E;
+    SFRD_CUDA(cudaMemsetAsync(p->ws + p->off_W, 0, 6 * fld, s));   // W, W2, U, F1, F2, F3 (padding stays 0)
+    if (p->dtype == SFRD_F32) {
+        SFRD_CUDA(prepare_kernels<float>(*p));
+        SFRD_CUDA(launch_coef_init<float>(*p, s));
+    } else {
+        SFRD_CUDA(prepare_kernels<double>(*p));
+        SFRD_CUDA(launch_coef_init<double>(*p, s));
+    }
+    SFRD_CUDA(launch_set_clock(*p, 0.0, s));
+    // pageable sources: make sure the uploads are complete before the host vectors can change
+    SFRD_CUDA(cudaStreamSynchronize(s));
+    return SFRD_OK;
+}
+
+static cudaError_t step_direct(Plan* p, cudaStream_t s) {
+    return p->dtype == SFRD_F32 ? launch_step<float>(*p, s) : launch_step<double>(*p, s);
+}
+
+static int ensure_graph(Plan* p) {
+    if (p->step_exec) return SFRD_OK;
+    SFRD_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = step_direct(p, p->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e, "step capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    p->step_graph = graph;
+    SFRD_CUDA(cudaGraphInstantiate(&p->step_exec, graph, 0));
+    return SFRD_OK;
+}
+
+static bool use_graph() {
+    const char* v = std::getenv("SFRD_NO_GRAPH");
+    return !(v && v[0] == '1');
+}
+
+static int load(Plan* p, const void* u0, double t0) {
+    if (!p->ws) return SFRD_ENOWS;
+    if (!u0) return SFRD_EINVAL;
+    SFRD_CUDA(launch_set_clock(*p, t0, p->stream));
+    if (p->dtype == SFRD_F32) SFRD_CUDA(launch_load<float>(*p, u0, p->stream));
+    else SFRD_CUDA(launch_load<double>(*p, u0, p->stream));
+    p->loaded = true;
+    return SFRD_OK;
+}
+
+static int advance(Plan* p, int64_t nsteps) {
+    if (!p->ws) return SFRD_ENOWS;
+    if (!p->loaded) return SFRD_ESTATE;
+    if (nsteps < 0) return SFRD_EINVAL;
+    if (nsteps == 0) return SFRD_OK;
+    if (use_graph()) {
+        int rc = ensure_graph(p);
+        if (rc != SFRD_OK) return rc;
+        for (int64_t i = 0; i < nsteps; ++i) SFRD_CUDA(cudaGraphLaunch(p->step_exec, p->stream));
+    } else {
+        for (int64_t i = 0; i < nsteps; ++i) SFRD_CUDA(step_direct(p, p->stream));
+    }
+    return SFRD_OK;
+}
+
+static int store(Plan* p, void* u) {
+    if (!p->ws) return SFRD_ENOWS;
+    if (!p->loaded) return SFRD_ESTATE;
+    if (!u) return SFRD_EINVAL;
+    if (p->dtype == SFRD_F32) SFRD_CUDA(launch_store<float>(*p, u, p->stream));
+    else SFRD_CUDA(launch_store<double>(*p, u, p->stream));
+    return SFRD_OK;
+}
+
+}  // namespace sfrd
+
+using sfrd::Plan;
+
+struct sfrd_plan_s {
+    Plan p;
+};
+
+#define SFRD_CUDA_C(call)                                           \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return sfrd::cuda_fail(e_, #call);   \
+    } while (0)
+
+extern "C" {
+
+int sfrd_plan(sfrd_plan_t* out, const sfrd_grid* grid, int32_t bc, const double* alpha, const double* kappa,
+              double dt, int32_t dtype, const sfrd_reaction* reaction) {
+    if (!out) return SFRD_EINVAL;
+    *out = nullptr;
+    Plan* p = nullptr;
+    int rc = sfrd::create(&p, grid, bc, alpha, kappa, dt, dtype, reaction);
+    if (rc != SFRD_OK) return rc;
+    sfrd_plan_s* h = new (std::nothrow) sfrd_plan_s();
+    if (!h) {
+        delete p;
+        return SFRD_EINVAL;
+    }
+    h->p = *p;
+    delete p;
+    *out = h;
+    return SFRD_OK;
+}
+
+int sfrd_workspace_bytes(sfrd_plan_t plan, size_t* bytes) {
+    if (!plan || !bytes) return SFRD_EINVAL;
+    *bytes = plan->p.ws_bytes;
+    return SFRD_OK;
+}
+
+int sfrd_get_info(sfrd_plan_t plan, sfrd_info* info) {
+    if (!plan || !info) return SFRD_EINVAL;
+    const Plan& p = plan->p;
+    std::memset(info, 0, sizeof(*info));
+    info->dim = p.dim;
+    info->bc = p.bc;
+    info->dtype = p.dtype;
+    info->nspecies = p.S;
+    for (int d = 0; d < 3; ++d) {
+        info->n[d] = d < p.dim ? p.n[d] : 1;
+        info->fft_len[d] = d < p.dim ? p.M[d] : 1;
+    }
+    info->dof = p.dense * p.S;
+    info->kernels_per_step = sfrd::kernels_per_step(p);
+    info->workspace_bytes = p.ws_bytes;
+    return SFRD_OK;
+}
+
+int sfrd_bind(sfrd_plan_t plan, void* workspace, size_t bytes, void* stream) {
+    if (!plan) return SFRD_EINVAL;
+    return sfrd::bind(&plan->p, workspace, bytes, stream);
+}
+
+int sfrd_load(sfrd_plan_t plan, const void* u0, double t0) {
+    if (!plan) return SFRD_EINVAL;
+    return sfrd::load(&plan->p, u0, t0);
+}
+
+int sfrd_advance(sfrd_plan_t plan, int64_t nsteps) {
+    if (!plan) return SFRD_EINVAL;
+    return sfrd::advance(&plan->p, nsteps);
+}
+
+int sfrd_store(sfrd_plan_t plan, void* u) {
+    if (!plan) return SFRD_EINVAL;
+    return sfrd::store(&plan->p, u);
+}
+
+int sfrd_run(sfrd_plan_t plan, void* u, double t0, int64_t nsteps) {
+    if (!plan) return SFRD_EINVAL;
+    if (nsteps < 0) return SFRD_EINVAL;
+    int rc = sfrd::load(&plan->p, u, t0);
+    if (rc != SFRD_OK) return rc;
+    rc = sfrd::advance(&plan->p, nsteps);
+    if (rc != SFRD_OK) return rc;
+    return sfrd::store(&plan->p, u);
+}
+
+int sfrd_step(sfrd_plan_t plan, void* u, double t) { return sfrd_run(plan, u, t, 1); }
+
+int sfrd_run_host(sfrd_plan_t plan, const void* u_in, void* u_out, double t0, int64_t nsteps) {
+    if (!plan || !u_in || !u_out) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (!p.ws) return SFRD_ENOWS;
+    const size_t bytes = (size_t)p.S * p.dense * p.esize;
+    void* D = p.ws + p.off_D;
+    cudaError_t e = cudaMemcpyAsync(D, u_in, bytes, cudaMemcpyHostToDevice, p.stream);
+    if (e != cudaSuccess) return sfrd::cuda_fail(e, "cudaMemcpyAsync(H2D)");
+    int rc = sfrd_run(plan, D, t0, nsteps);
+    if (rc != SFRD_OK) return rc;
+    e = cudaMemcpyAsync(u_out, D, bytes, cudaMemcpyDeviceToHost, p.stream);
+    if (e != cudaSuccess) return sfrd::cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    e = cudaStreamSynchronize(p.stream);
+    if (e != cudaSuccess) return sfrd::cuda_fail(e, "cudaStreamSynchronize");
+    return SFRD_OK;
+}
+
+int sfrd_forward(sfrd_plan_t plan, const void* u, void* uhat) {
+    if (!plan || !u || !uhat) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (!p.ws) return SFRD_ENOWS;
+    cudaError_t e = p.dtype == SFRD_F32 ? sfrd::launch_forward<float>(p, u, uhat, p.stream)
+                                        : sfrd::launch_forward<double>(p, u, uhat, p.stream);
+    return e == cudaSuccess ? SFRD_OK : sfrd::cuda_fail(e, "sfrd_forward");
+}
+
+int sfrd_inverse(sfrd_plan_t plan, const void* uhat, void* u) {
+    if (!plan || !u || !uhat) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (!p.ws) return SFRD_ENOWS;
+    cudaError_t e = p.dtype == SFRD_F32 ? sfrd::launch_inverse<float>(p, uhat, u, p.stream)
+                                        : sfrd::launch_inverse<double>(p, uhat, u, p.stream);
+    return e == cudaSuccess ? SFRD_OK : sfrd::cuda_fail(e, "sfrd_inverse");
+}
+
+int sfrd_coefficients(sfrd_plan_t plan, int32_t which, void* out) {
+    if (!plan || !out || which < 0 || which > 5) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (!p.ws) return SFRD_ENOWS;
+    cudaError_t e = p.dtype == SFRD_F32 ? sfrd::launch_coef_copy<float>(p, which, out, p.stream)
+                                        : sfrd::launch_coef_copy<double>(p, which, out, p.stream);
+    return e == cudaSuccess ? SFRD_OK : sfrd::cuda_fail(e, "sfrd_coefficients");
+}
+
+int sfrd_profile_step(sfrd_plan_t plan, int32_t cap, float* ms, int32_t* kind) {
+    if (!plan || !ms || !kind || cap < 1) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (!p.ws) return SFRD_ENOWS;
+    if (!p.loaded) return SFRD_ESTATE;
+    const int n = sfrd::kernels_per_step(p) < cap ? sfrd::kernels_per_step(p) : cap;
+    std::vector<cudaEvent_t> ev(n + 1, nullptr);
+    std::vector<int> kinds(n, -1);
+    for (auto& e : ev) SFRD_CUDA_C(cudaEventCreate(&e));
+    cudaError_t e = p.dtype == SFRD_F32 ? sfrd::launch_step_profiled<float>(p, p.stream, ev.data(), kinds.data(), n)
+                                        : sfrd::launch_step_profiled<double>(p, p.stream, ev.data(), kinds.data(), n);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[n]);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+        kind[i] = kinds[i];
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    return e == cudaSuccess ? SFRD_OK : sfrd::cuda_fail(e, "sfrd_profile_step");
+}
+
+void sfrd_destroy(sfrd_plan_t plan) {
+    if (!plan) return;
+    sfrd::drop_graph(&plan->p);
+    if (plan->p.cap_stream) cudaStreamDestroy(plan->p.cap_stream);
+    delete plan;
+}
+
+const char* sfrd_strerror(int code) {
+    switch (code) {
+        case SFRD_OK: return "ok";
+        case SFRD_EINVAL: return "invalid argument";
+        case SFRD_EUNSUPPORTED: return "unsupported problem size or dimension";
+        case SFRD_ENOWS: return "workspace missing, too small or misaligned";
+        case SFRD_ECUDA: return "CUDA runtime error";
+        case SFRD_ENONFINITE: return "non-finite value in the state";
+        case SFRD_ESTATE: return "call out of order (no state loaded)";
+        default: return "unknown error";
+    }
+}
+
+const char* sfrd_last_error(void) { return sfrd::g_last_error.c_str(); }
+
+}  // extern "C"

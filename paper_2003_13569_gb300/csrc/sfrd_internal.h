@@ -1,0 +1,149 @@
+// Internal declarations shared by the host plan code and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sfrd.h"
+
+namespace sfrd {
+
+constexpr int kMaxStages = 16;
+constexpr int kMaxFFT = 1024;   // longest complex FFT along one axis
+constexpr int kThreads = 256;   // threads per block of every transform pass
+
+// Per-axis description handed to kernels by value.
+struct AxisDev {
+    int n;        // unknowns along the axis
+    int N;        // intervals
+    int M;        // complex FFT length: N (periodic) or 2N (Dirichlet/Neumann extension)
+    int bc;       // SFRD_BC_*
+    int nst;      // radix stages
+    int radix[kMaxStages];   // DIF order; DIT runs them reversed
+    const void* tw;          // omega_M^k = exp(-2 pi i k / M), k < M, in the run precision
+    const int* perm;         // extension index -> buffer slot after DIF (= DIT input slot)
+    int node0;               // grid node of unknown 0 (1 for Dirichlet, else 0)
+    double lo, h;            // node coordinate = lo + (node0 + i) h
+};
+
+struct ReactDev {
+    int kind;
+    int S;
+    double p[8];
+    double off[2];
+};
+
+// Device-resident clock: t_k = t0 + k tau (Algorithm 1).
+struct Clock {
+    double t0;
+    long long k;
+};
+
+// Transform pass kinds.
+enum PassMode {
+    MODE_PLAIN = 0,  // one transform along the axis, out = scale * T(in)
+    MODE_T0 = 1,     // slow axis: F = T(in); U <- F; out = T(U)/C
+    MODE_TA = 2,     // slow axis: F1 <- T(in); out = T(Q U + phi F1)/C
+    MODE_TB = 3,     // slow axis: F2 <- T(in); out = T(Q U + phi F2)/C
+    MODE_TC = 4,     // slow axis: F3 <- T(in); out = T(Q(Q U + phi F1) + phi(2F3 - F1))/C
+    MODE_TD = 5,     // slow axis: U <- R U + phi1 F1 + phi2 (F2+F3) + phi3 T(in); out = T(U)/C
+    MODE_REACT = 6,  // contiguous axis: out = T(f(T(in)))
+};
+
+// Pass kinds reported by the per-launch profile of one step.
+enum PassKind { PASS_X = 0, PASS_MID = 1, PASS_SLOW_A = 2, PASS_SLOW_B = 3, PASS_SLOW_C = 4, PASS_SLOW_D = 5 };
+
+template <typename T>
+struct ColArgs {
+    const T* in;
+    T* out;
+    long long in_offB;    // element offset from real column A to real column B
+    long long in_sAxis;   // stride along the transformed axis
+    long long in_sOther;  // stride of the blockIdx.y coordinate
+    long long out_offB, out_sAxis, out_sOther;   // same for the output array
+    int in_xlim;          // columns x < in_xlim are loaded (others read as 0)
+    int out_xlim;         // columns x < out_xlim are stored
+    int xw;               // x advance per blockIdx.x
+    int bshift;           // column of line B minus column of line A (0: other species; CC: same species)
+    double scale;         // output scale (plain mode)
+    double invC;          // 1/C for the slow-axis inverse (T modes)
+    T* U;
+    T* F1;
+    T* F2;
+    T* F3;
+    const T* CQ;          // interleaved (Q13, phi) pairs
+    const T* CR;          // interleaved (R13, phi1, phi2, phi3) quads
+    Clock* clock;         // TD advances k
+    AxisDev ax;
+};
+
+template <typename T>
+struct XArgs {
+    const T* in;
+    T* out;
+    long long in_offB, out_offB;      // element offset from row A to row B
+    long long in_pitch, out_pitch;    // row strides
+    int rows;                         // (z, y) rows per species
+    int out_fill;                     // zero-fill columns n..out_fill-1 of each output row
+    int S;
+    int ny;                           // rows -> (y, z) for coordinates
+    double tau, stage_frac;           // reaction time = t0 + (k + stage_frac) tau
+    const Clock* clock;
+    AxisDev ax, ay, az;
+    ReactDev re;
+};
+
+// Host-side plan.
+struct Plan {
+    int dim = 0, bc = 0, dtype = 0, S = 0;
+    int64_t Nint[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    int n[3] = {1, 1, 1};      // unknowns (x, y, z)
+    int M[3] = {1, 1, 1};
+    int pitch = 0;             // internal row pitch (elements), multiple of 4
+    long long plane = 0;       // internal elements per species: n_z * n_y * pitch
+    long long dense = 0;       // dense elements per species: n_z * n_y * n_x
+    double alpha[2] = {0, 0}, kappa[2] = {0, 0};
+    double dt = 0;
+    ReactDev re{};
+    int CC = 16;               // complex columns per tile
+    size_t esize = 8;
+
+    // host tables (kept alive for async uploads)
+    std::vector<double> lam[3];
+    std::vector<double> tw64[3];   // interleaved re, im
+    std::vector<float> tw32[3];
+    std::vector<int> perm[3];
+    std::vector<int> radix[3];
+
+    // workspace layout (byte offsets)
+    size_t off_W = 0, off_W2 = 0, off_U = 0, off_F1 = 0, off_F2 = 0, off_F3 = 0;
+    size_t off_CQ = 0, off_CR = 0, off_clock = 0, off_D = 0;
+    size_t off_tw[3] = {0, 0, 0}, off_perm[3] = {0, 0, 0}, off_lam[3] = {0, 0, 0};
+    size_t ws_bytes = 0;
+
+    char* ws = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    cudaGraph_t step_graph = nullptr;
+    bool loaded = false;
+};
+
+// Launchers (sfrd_passes_*.cu), templated on the run precision.
+template <typename T> cudaError_t launch_step(Plan& p, cudaStream_t s);
+template <typename T> cudaError_t launch_step_profiled(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind, int cap);
+template <typename T> cudaError_t launch_load(Plan& p, const void* u0, cudaStream_t s);
+template <typename T> cudaError_t launch_store(Plan& p, void* u, cudaStream_t s);
+template <typename T> cudaError_t launch_forward(Plan& p, const void* u, void* uhat, cudaStream_t s);
+template <typename T> cudaError_t launch_inverse(Plan& p, const void* uhat, void* u, cudaStream_t s);
+template <typename T> cudaError_t launch_coef_init(Plan& p, cudaStream_t s);
+template <typename T> cudaError_t launch_coef_copy(Plan& p, int which, void* out, cudaStream_t s);
+template <typename T> cudaError_t prepare_kernels(const Plan& p);
+cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s);
+
+int kernels_per_step(const Plan& p);
+
+}  // namespace sfrd
