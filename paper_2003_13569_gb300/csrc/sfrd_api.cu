@@ -188,8 +188,11 @@ static int create(Plan** out, const sfrd_grid* g, int bc, const double* alpha, c
 
     // FP64 tables: eigenvalues (Section 3.1), twiddles omega_M^k, DIF slot permutation
     for (int d = 0; d < 3; ++d) {
-        if (d >= g->dim) {
+        if (d >= g->dim) {        // absent axis: one mode with eigenvalue 0, identity transform
             p->lam[d].assign(1, 0.0);
+            p->tw64[d] = {1.0, 0.0};
+            p->tw32[d] = {1.0f, 0.0f};
+            p->perm[d].assign(1, 0);
             continue;
         }
         const long long N = p->Nint[d];
