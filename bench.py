@@ -106,7 +106,7 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Algorithmic HBM words per unknown (per species element) of each pass kind; see the design doc.
+# Algorithmic HBM words per unknown (per species element) of each pass kind (fixed pass model).
 # x pass: read + write the field (the reaction needs no extra traffic);
 # middle pass: read + write; slow passes: field in/out + stored spectra + coefficients.
 WORDS = {0: 2, 1: 2, 2: 6, 3: 6, 4: 7, 5: 11}

@@ -1,0 +1,324 @@
+// Register FFT engine for power-of-two axis lengths N (16 <= N <= 1024).
+//
+// Each real transform of the solver (Section 3.1: Hartley for periodic axes,
+// DST-I for Dirichlet, DCT-I for Neumann) is computed from ONE complex FFT of
+// length N carrying two real lines (real part = line A, imaginary part = B):
+//
+//   periodic:  z_j = x_j;                                    T_k = R_k + I_k, T_{N-k} = R_k - I_k
+//   Dirichlet: z_j = s_j (x_j + x_{N-j}) + (x_j - x_{N-j})/2 T_{2k} = I_k,  T_{2k+1} = T_{2k-1} + R_k
+//   Neumann:   z_j = (x_j + x_{N-j})/2 - s_j (x_j - x_{N-j}) T_{2k} = R_k,  T_{2k+1} = T_{2k-1} + I_k
+// with s_j = sin(j pi / N), x the line on grid nodes (x_0 = x_N = 0 for
+// Dirichlet), and R_k - i I_k the DFT of the pre-processed real line, unpacked
+// from the packed complex DFT.  The odd-index outputs of DST-I / DCT-I follow
+// from a running sum, done as a two-level prefix sum over the half spectrum;
+// its anchor is T_1 = R_0 / 2 (Dirichlet) or T_1 = (x_0 - x_N)/2 +
+// sum_j x_j cos(j pi / N) (Neumann).  These are the classical real-FFT
+// pre/post-processings of the sine and cosine transforms: pairing j with N-j
+// splits the kernel sin(pi j k'/N) (or cos) into the even part, a plain real
+// DFT, and the odd part, whose products with s_j telescope in k'.
+//
+// The complex FFT is a two-step decomposition N = R1 x R2 entirely in
+// registers (j = R2 n1 + n2, k = k1 + R1 k2): step 1 owns n2 and does a
+// DFT-R1 over n1 followed by the twiddles omega_N^{n2 k1}; one shared-memory
+// exchange; step 2 owns k1 and does a DFT-R2 over n2, writing X in natural
+// order into the same slots it read.  All sizes and loop bounds are
+// compile-time constants.
+//
+// Tile: CC columns (lane c), G = 256 / CC groups (g).  Shared memory holds one
+// buffer of max(n, N) rows x (CC + 1) complex: it is the value buffer V (row =
+// unknown index) before the pre-processing and after the post-processing, and
+// the FFT buffer Z in between; barriers separate the two uses.
+#pragma once
+
+#include "engine.cuh"
+
+namespace sfrd {
+namespace v2 {
+
+// ---- compile-time trigonometry (Taylor series on a reduced argument) -------------
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+constexpr double ce_sin_small(double x) {
+    double x2 = x * x, t = x, s = x;
+    for (int i = 1; i < 16; ++i) {
+        t *= -x2 / ((2.0 * i) * (2.0 * i + 1.0));
+        s += t;
+    }
+    return s;
+}
+
+constexpr double ce_cos_small(double x) {
+    double x2 = x * x, t = 1.0, s = 1.0;
+    for (int i = 1; i < 16; ++i) {
+        t *= -x2 / ((2.0 * i - 1.0) * (2.0 * i));
+        s += t;
+    }
+    return s;
+}
+
+struct CS {
+    double c, s;
+};
+
+// cos and sin of 2 pi m / R, argument reduced exactly on the integers.
+constexpr CS ce_cs2pi(long m, long R) {
+    long r = m % R;
+    if (r < 0) r += R;
+    const long q = (4 * r) / R;
+    const long rem = 4 * r - q * R;
+    double c0 = 0, s0 = 0;
+    if (2 * rem <= R) {
+        const double ph = (kPi / 2) * (double)rem / (double)R;
+        c0 = ce_cos_small(ph);
+        s0 = ce_sin_small(ph);
+    } else {
+        const double ph = (kPi / 2) * (double)(R - rem) / (double)R;
+        c0 = ce_sin_small(ph);
+        s0 = ce_cos_small(ph);
+    }
+    switch (q) {
+        case 0: return CS{c0, s0};
+        case 1: return CS{-s0, c0};
+        case 2: return CS{-c0, -s0};
+        default: return CS{s0, -c0};
+    }
+}
+
+// omega_32^m = exp(-2 pi i m / 32), used by the in-register DFTs of length 16 and 32.
+#define SFRD_W32F(m) {(float)ce_cs2pi(m, 32).c, (float)(-ce_cs2pi(m, 32).s)}
+#define SFRD_W32D(m) {ce_cs2pi(m, 32).c, -ce_cs2pi(m, 32).s}
+static __constant__ float2 kW32f[32] = {
+    SFRD_W32F(0),  SFRD_W32F(1),  SFRD_W32F(2),  SFRD_W32F(3),  SFRD_W32F(4),  SFRD_W32F(5),  SFRD_W32F(6),
+    SFRD_W32F(7),  SFRD_W32F(8),  SFRD_W32F(9),  SFRD_W32F(10), SFRD_W32F(11), SFRD_W32F(12), SFRD_W32F(13),
+    SFRD_W32F(14), SFRD_W32F(15), SFRD_W32F(16), SFRD_W32F(17), SFRD_W32F(18), SFRD_W32F(19), SFRD_W32F(20),
+    SFRD_W32F(21), SFRD_W32F(22), SFRD_W32F(23), SFRD_W32F(24), SFRD_W32F(25), SFRD_W32F(26), SFRD_W32F(27),
+    SFRD_W32F(28), SFRD_W32F(29), SFRD_W32F(30), SFRD_W32F(31)};
+static __constant__ double2 kW32d[32] = {
+    SFRD_W32D(0),  SFRD_W32D(1),  SFRD_W32D(2),  SFRD_W32D(3),  SFRD_W32D(4),  SFRD_W32D(5),  SFRD_W32D(6),
+    SFRD_W32D(7),  SFRD_W32D(8),  SFRD_W32D(9),  SFRD_W32D(10), SFRD_W32D(11), SFRD_W32D(12), SFRD_W32D(13),
+    SFRD_W32D(14), SFRD_W32D(15), SFRD_W32D(16), SFRD_W32D(17), SFRD_W32D(18), SFRD_W32D(19), SFRD_W32D(20),
+    SFRD_W32D(21), SFRD_W32D(22), SFRD_W32D(23), SFRD_W32D(24), SFRD_W32D(25), SFRD_W32D(26), SFRD_W32D(27),
+    SFRD_W32D(28), SFRD_W32D(29), SFRD_W32D(30), SFRD_W32D(31)};
+#undef SFRD_W32F
+#undef SFRD_W32D
+
+template <typename C> __device__ __forceinline__ C w32(int m);
+template <> __device__ __forceinline__ float2 w32<float2>(int m) { return kW32f[m]; }
+template <> __device__ __forceinline__ double2 w32<double2>(int m) { return kW32d[m]; }
+
+// ---- in-register DFTs of length 2..32 (natural order in and out) -----------------
+
+template <int R, typename C> struct RDft {
+    static __device__ __forceinline__ void run(C* a) { Dft<R, C>::run(a); }
+};
+
+// R = Ra * Rb four-step: j = Rb j1 + j2, k = k1 + Ra k2.
+template <int R, int Ra, typename C> struct FourStep {
+    static constexpr int Rb = R / Ra;
+    static __device__ __forceinline__ void run(C* a) {
+        C t[R];
+#pragma unroll
+        for (int j2 = 0; j2 < Rb; ++j2) {
+            C u[Ra];
+#pragma unroll
+            for (int j1 = 0; j1 < Ra; ++j1) u[j1] = a[Rb * j1 + j2];
+            RDft<Ra, C>::run(u);
+#pragma unroll
+            for (int k1 = 0; k1 < Ra; ++k1)
+                t[j2 * Ra + k1] = (j2 * k1 == 0) ? u[k1] : cmul(u[k1], w32<C>((j2 * k1 * (32 / R)) % 32));
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < Ra; ++k1) {
+            C w[Rb];
+#pragma unroll
+            for (int j2 = 0; j2 < Rb; ++j2) w[j2] = t[j2 * Ra + k1];
+            RDft<Rb, C>::run(w);
+#pragma unroll
+            for (int k2 = 0; k2 < Rb; ++k2) a[k1 + Ra * k2] = w[k2];
+        }
+    }
+};
+
+template <typename C> struct RDft<16, C> {
+    static __device__ __forceinline__ void run(C* a) { FourStep<16, 4, C>::run(a); }
+};
+template <typename C> struct RDft<32, C> {
+    static __device__ __forceinline__ void run(C* a) { FourStep<32, 8, C>::run(a); }
+};
+
+// ---- the line engine ----------------------------------------------------------------
+
+template <int N> struct Split;
+template <> struct Split<16> { static constexpr int R1 = 4, R2 = 4; };
+template <> struct Split<32> { static constexpr int R1 = 4, R2 = 8; };
+template <> struct Split<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct Split<128> { static constexpr int R1 = 8, R2 = 16; };
+template <> struct Split<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct Split<512> { static constexpr int R1 = 16, R2 = 32; };
+template <> struct Split<1024> { static constexpr int R1 = 32, R2 = 32; };
+
+// Columns per tile for a power-of-two axis length.
+template <typename T, int N> struct TileCC { static constexpr int value = cc_for(sizeof(T) == 8, N); };
+
+template <typename T, int N, int CC>
+struct Eng {
+    using C = typename Cx<T>::type;
+    static constexpr int G = kThreads / CC;
+    static constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2;
+    static constexpr int LD = CC + 1;
+    static constexpr int H = N / 2;
+    static constexpr int CH = (H + G - 1) / G;      // half-spectrum pairs per group
+    static constexpr int NO1 = (R2 + G - 1) / G;    // step-1 owners per thread
+    static constexpr int NO2 = (R1 + G - 1) / G;    // step-2 owners per thread
+    static constexpr int ROWS = N + 1;              // buffer rows (n <= N + 1)
+
+    static constexpr size_t smem_bytes() {
+        return (size_t)ROWS * LD * sizeof(C) + (size_t)2 * G * CC * sizeof(C);
+    }
+
+    // Pre-processed input z_j of the packed DFT, read from the value buffer.
+    static __device__ __forceinline__ C pre(const C* V, int bc, int j, int c, const C* __restrict__ tw2,
+                                            C& anchor) {
+        if (bc == SFRD_BC_PERIODIC) return V[j * LD + c];
+        const C w = __ldg(tw2 + j);       // (cos(j pi/N), -sin(j pi/N))
+        const T s = -w.y;
+        if (bc == SFRD_BC_DIRICHLET) {
+            if (j == 0) return czero<C>();
+            const C xj = V[(j - 1) * LD + c], xm = V[(N - j - 1) * LD + c];
+            C z;
+            z.x = s * (xj.x + xm.x) + (T)0.5 * (xj.x - xm.x);
+            z.y = s * (xj.y + xm.y) + (T)0.5 * (xj.y - xm.y);
+            return z;
+        }
+        const C xj = V[j * LD + c], xm = V[(N - j) * LD + c];
+        if (j == 0) {
+            anchor.x += (T)0.5 * (xj.x - xm.x);
+            anchor.y += (T)0.5 * (xj.y - xm.y);
+        } else {
+            anchor.x += xj.x * w.x;
+            anchor.y += xj.y * w.x;
+        }
+        C z;
+        z.x = (T)0.5 * (xj.x + xm.x) - s * (xj.x - xm.x);
+        z.y = (T)0.5 * (xj.y + xm.y) - s * (xj.y - xm.y);
+        return z;
+    }
+
+    // V (natural, unknown index) -> pre-processing -> DFT_N -> Z (natural order).
+    // Entry: V complete (after a barrier).  Exit: Z complete (after a barrier).
+    // red2[g][c] receives this thread's part of the Neumann anchor.
+    static __device__ __forceinline__ void forward(C* buf, C* red2, int bc, const C* __restrict__ twN, int twstride,
+                                                   const C* __restrict__ tw2, int c, int g) {
+        C a[NO1][R1];
+        C anchor = czero<C>();
+#pragma unroll
+        for (int o = 0; o < NO1; ++o) {
+            const int n2 = g + o * G;
+            if (R2 % G == 0 || n2 < R2) {
+#pragma unroll
+                for (int n1 = 0; n1 < R1; ++n1) a[o][n1] = pre(buf, bc, R2 * n1 + n2, c, tw2, anchor);
+                RDft<R1, C>::run(a[o]);
+#pragma unroll
+                for (int k1 = 1; k1 < R1; ++k1) a[o][k1] = cmul(a[o][k1], __ldg(twN + (n2 * k1) * twstride));
+            }
+        }
+        red2[g * CC + c] = anchor;
+        __syncthreads();   // all reads of V done: the buffer becomes Z
+#pragma unroll
+        for (int o = 0; o < NO1; ++o) {
+            const int n2 = g + o * G;
+            if (R2 % G == 0 || n2 < R2) {
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) buf[(n2 * R1 + k1) * LD + c] = a[o][k1];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int o = 0; o < NO2; ++o) {
+            const int k1 = g + o * G;
+            if (R1 % G == 0 || k1 < R1) {
+                C b[R2];
+#pragma unroll
+                for (int n2 = 0; n2 < R2; ++n2) b[n2] = buf[(n2 * R1 + k1) * LD + c];
+                RDft<R2, C>::run(b);
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) buf[(k1 + R1 * k2) * LD + c] = b[k2];
+            }
+        }
+        __syncthreads();
+    }
+
+    // Z (natural) -> transform values; sink(i, value) is called for every unknown i
+    // of this thread's output range after a barrier (so the sink may write V).
+    template <class Sink>
+    static __device__ __forceinline__ void post(C* buf, C* red, const C* red2, int bc, int c, int g, Sink&& sink) {
+        C ev[CH], od[CH];   // even-index outputs, running odd-index partial sums
+        C run = czero<C>();
+        const int k0 = g * CH;
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+            const int k = k0 + t;
+            if (k < H) {
+                const C zk = buf[k * LD + c];
+                const C zm = buf[((N - k) & (N - 1)) * LD + c];
+                C Rk, Ik;
+                Rk.x = (T)0.5 * (zk.x + zm.x);
+                Rk.y = (T)0.5 * (zk.y + zm.y);
+                Ik.x = (T)0.5 * (zm.y - zk.y);
+                Ik.y = (T)0.5 * (zk.x - zm.x);
+                if (bc == SFRD_BC_PERIODIC) {
+                    ev[t] = cadd(Rk, Ik);     // T_k
+                    od[t] = csub(Rk, Ik);     // T_{N-k}
+                } else if (bc == SFRD_BC_DIRICHLET) {
+                    ev[t] = Ik;
+                    C d = Rk;
+                    if (k == 0) { d.x *= (T)0.5; d.y *= (T)0.5; }
+                    run = cadd(run, d);
+                    od[t] = run;
+                } else {
+                    ev[t] = Rk;
+                    C d = Ik;
+                    if (k == 0) {
+                        d = czero<C>();
+#pragma unroll 4
+                        for (int q = 0; q < G; ++q) d = cadd(d, red2[q * CC + c]);
+                    }
+                    run = cadd(run, d);
+                    od[t] = run;
+                }
+            }
+        }
+        C nyq = czero<C>();
+        if (bc != SFRD_BC_DIRICHLET && g == G - 1) {
+            const C zh = buf[H * LD + c];     // k = N/2: R = Re, I = 0 for both lines
+            nyq = zh;
+        }
+        if (bc != SFRD_BC_PERIODIC) red[g * CC + c] = run;
+        __syncthreads();   // all reads of Z done: the buffer becomes V
+        C pre_sum = czero<C>();
+        if (bc != SFRD_BC_PERIODIC) {
+            for (int q = 0; q < g; ++q) pre_sum = cadd(pre_sum, red[q * CC + c]);
+        }
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+            const int k = k0 + t;
+            if (k < H) {
+                if (bc == SFRD_BC_PERIODIC) {
+                    sink(k, ev[t]);
+                    if (k != 0) sink(N - k, od[t]);
+                } else if (bc == SFRD_BC_DIRICHLET) {
+                    if (k != 0) sink(2 * k - 1, ev[t]);
+                    sink(2 * k, cadd(pre_sum, od[t]));
+                } else {
+                    sink(2 * k, ev[t]);
+                    sink(2 * k + 1, cadd(pre_sum, od[t]));
+                }
+            }
+        }
+        if (bc != SFRD_BC_DIRICHLET && g == G - 1) sink(bc == SFRD_BC_PERIODIC ? H : N, nyq);
+    }
+};
+
+}  // namespace v2
+}  // namespace sfrd

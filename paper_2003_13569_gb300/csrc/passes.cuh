@@ -20,71 +20,9 @@
 #pragma once
 
 #include "engine.cuh"
+#include "reaction.cuh"
 
 namespace sfrd {
-
-// ---- reaction terms (Section 5.2; parameters as documented in sfrd.h) -----------
-
-template <typename T>
-__device__ __forceinline__ void react2(const ReactDev& re, T u, T v, T& fu, T& fv) {
-    switch (re.kind) {
-        case SFRD_REACT_FHN: {
-            const T mu = (T)re.p[0], eps = (T)re.p[1], beta = (T)re.p[2], gam = (T)re.p[3], del = (T)re.p[4];
-            fu = u * ((T)1 - u) * (u - mu) - v;
-            fv = eps * (beta * u - gam * v - del);
-        } break;
-        case SFRD_REACT_GRAY_SCOTT: {
-            const T F = (T)re.p[0], K = (T)re.p[1];
-            const T uvv = u * v * v;
-            fu = -uvv + F * ((T)1 - u);
-            fv = uvv - (F + K) * v;
-        } break;
-        case SFRD_REACT_SCHNAKENBERG: {
-            const T g = (T)re.p[0], a = (T)re.p[1], b = (T)re.p[2];
-            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
-            const T uuv = U * U * V;
-            fu = g * (a - U + uuv);
-            fv = g * (b - uuv);
-        } break;
-        case SFRD_REACT_GIERER_MEINHARDT: {
-            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
-            fu = (T)re.p[0] * U * U / V - (T)re.p[1] * U;
-            fv = (T)re.p[2] * U * U - (T)re.p[3] * V;
-        } break;
-        case SFRD_REACT_LINEAR:
-            fu = (T)re.p[0] * u;
-            fv = (T)re.p[0] * v;
-            break;
-        default:
-            fu = 0;
-            fv = 0;
-    }
-}
-
-// Single-species terms; x, y are node coordinates, t the stage time.
-template <typename T>
-__device__ __forceinline__ T react1(const ReactDev& re, T u, double x, double y, double t) {
-    switch (re.kind) {
-        case SFRD_REACT_LINEAR:
-            return (T)re.p[0] * u;
-        case SFRD_REACT_HUXLEY_MMS: {
-            // Example 2: exact solution t^alpha cos^3(2 pi x) cos^3(2 pi y); p = [alpha, k1..k4]
-            // with Phi = k1 c1x c1y + k2 c3x c1y + k3 c1x c3y + k4 c3x c3y, cNz = cos(2 N pi z).
-            const double al = re.p[0];
-            const double c1x = cospi(2.0 * x), c1y = cospi(2.0 * y);
-            const double c3x = cospi(6.0 * x), c3y = cospi(6.0 * y);
-            const double g = c1x * c1x * c1x * c1y * c1y * c1y;
-            const double Phi = re.p[1] * c1x * c1y + re.p[2] * c3x * c1y + re.p[3] * c1x * c3y + re.p[4] * c3x * c3y;
-            const double ta = t > 0 ? pow(t, al) : 0.0;
-            const double dta = t > 0 ? al * pow(t, al - 1.0) : 0.0;
-            const double w = ta * g;
-            const double src = dta * g + ta * Phi - w * (1.0 - w) * (w - 1.0);
-            return u * ((T)1 - u) * (u - (T)1) + (T)src;
-        }
-        default:
-            return 0;
-    }
-}
 
 // Value of the transform at unknown k from a DFT output held in slot order.
 template <typename C, bool PERM>
@@ -458,7 +396,16 @@ static cudaError_t dispatch_x(const Plan& p, const XArgs<T>& a, int mode, dim3 g
 
 template <typename T>
 cudaError_t prepare_kernels(const Plan& p) {
-    (void)p;
+    for (int d = 0; d < p.dim; ++d) {
+        if (!p.v2[d]) continue;
+        switch (p.Nint[d]) {
+            case 64: SFRD_TRY((v2::prepare2<T, 64>())); break;
+            case 128: SFRD_TRY((v2::prepare2<T, 128>())); break;
+            case 256: SFRD_TRY((v2::prepare2<T, 256>())); break;
+            case 512: SFRD_TRY((v2::prepare2<T, 512>())); break;
+            default: SFRD_TRY((v2::prepare2<T, 1024>())); break;
+        }
+    }
     SFRD_TRY((prepare_cc<T, CCs<T>::a>()));
     SFRD_TRY((prepare_cc<T, CCs<T>::b>()));
     return prepare_cc<T, CCs<T>::c>();
@@ -494,10 +441,12 @@ static cudaError_t run_col(const Plan& p, int d, int mode, const Arr<T>& in, con
     a.in = in.ptr;
     a.out = const_cast<T*>(out.ptr);
     const bool two = p.S == 2;
-    a.bshift = two ? 0 : p.CC;
-    a.xw = two ? p.CC : 2 * p.CC;
-    a.in_offB = two ? in.plane : p.CC;
-    a.out_offB = two ? out.plane : p.CC;
+    const bool use2 = p.v2[d];
+    const int cc = use2 ? v2::cc_for(sizeof(T) == 8, (int)p.Nint[d]) : p.CC;
+    a.bshift = two ? 0 : cc;
+    a.xw = two ? cc : 2 * cc;
+    a.in_offB = two ? in.plane : cc;
+    a.out_offB = two ? out.plane : cc;
     int gy = 1;
     if (d == 2) {          // z in 3D: blockIdx.y = y
         a.in_sAxis = (long long)ny * in.pitch;
@@ -534,6 +483,15 @@ static cudaError_t run_col(const Plan& p, int d, int mode, const Arr<T>& in, con
     a.ax = axis_dev<T>(p, d);
     const int xlim = in.xlim > out.xlim ? in.xlim : out.xlim;
     dim3 grid((xlim + a.xw - 1) / a.xw, gy, 1);
+    if (use2) {
+        switch (p.Nint[d]) {
+            case 64: return v2::col2_launch<T, 64>(a, mode, grid, s);
+            case 128: return v2::col2_launch<T, 128>(a, mode, grid, s);
+            case 256: return v2::col2_launch<T, 256>(a, mode, grid, s);
+            case 512: return v2::col2_launch<T, 512>(a, mode, grid, s);
+            default: return v2::col2_launch<T, 1024>(a, mode, grid, s);
+        }
+    }
     return dispatch_col<T>(p, a, mode, grid, tile_smem<T>(p, d), s);
 }
 
@@ -544,11 +502,13 @@ static cudaError_t run_x(const Plan& p, int mode, const Arr<T>& in, const Arr<T>
     a.in = in.ptr;
     a.out = const_cast<T*>(out.ptr);
     const bool two = p.S == 2;
+    const bool use2 = p.v2[0];
+    const int cc = use2 ? v2::cc_for(sizeof(T) == 8, (int)p.Nint[0]) : p.CC;
     a.S = p.S;
     a.in_pitch = in.pitch;
     a.out_pitch = out.pitch;
-    a.in_offB = two ? in.plane : (long long)p.CC * in.pitch;
-    a.out_offB = two ? out.plane : (long long)p.CC * out.pitch;
+    a.in_offB = two ? in.plane : (long long)cc * in.pitch;
+    a.out_offB = two ? out.plane : (long long)cc * out.pitch;
     a.rows = p.n[1] * p.n[2];
     a.out_fill = out_fill;
     a.ny = p.n[1];
@@ -559,8 +519,17 @@ static cudaError_t run_x(const Plan& p, int mode, const Arr<T>& in, const Arr<T>
     a.ay = axis_dev<T>(p, 1);
     if (p.dim == 3) a.az = axis_dev<T>(p, 2);
     a.re = p.re;
-    const int per = two ? p.CC : 2 * p.CC;
+    const int per = two ? cc : 2 * cc;
     dim3 grid((a.rows + per - 1) / per, 1, 1);
+    if (use2) {
+        switch (p.Nint[0]) {
+            case 64: return v2::x2_launch<T, 64>(a, mode, grid, s);
+            case 128: return v2::x2_launch<T, 128>(a, mode, grid, s);
+            case 256: return v2::x2_launch<T, 256>(a, mode, grid, s);
+            case 512: return v2::x2_launch<T, 512>(a, mode, grid, s);
+            default: return v2::x2_launch<T, 1024>(a, mode, grid, s);
+        }
+    }
     return dispatch_x<T>(p, a, mode, grid, tile_smem<T>(p, 0), s);
 }
 

@@ -1,0 +1,231 @@
+// Transform passes on the register FFT engine (power-of-two axis lengths).
+// Same pass structure, modes and arguments as passes.cuh; the per-axis real
+// transform is the length-N packed FFT of fft2.cuh instead of the generic
+// shared-memory FFT on the 2N extension.
+#pragma once
+
+#include "fft2.cuh"
+#include "reaction.cuh"
+
+namespace sfrd {
+namespace v2 {
+
+template <typename T, int N>
+struct TileOf {
+    static constexpr int CC = TileCC<T, N>::value;
+    using E = Eng<T, N, CC>;
+};
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(kThreads) col2_kernel(const ColArgs<T> a) {
+    constexpr int CC = TileOf<T, N>::CC;
+    using E = typename TileOf<T, N>::E;
+    using C = typename E::C;
+    constexpr int LD = E::LD, G = E::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* red = buf + E::ROWS * LD;
+    C* red2 = red + G * CC;
+    const int tid = threadIdx.x, c = tid % CC, g = tid / CC;
+    const AxisDev& ax = a.ax;
+    const int n = ax.n, bc = ax.bc;
+    const C* tw = static_cast<const C*>(ax.tw);
+    const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
+    const int xA = blockIdx.x * a.xw + c, xB = xA + a.bshift;
+    const long long other = blockIdx.y;
+
+    {
+        const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
+        const T* pA = a.in + other * a.in_sOther + xA;
+        for (int i = g; i < n; i += G) {
+            C z;
+            z.x = okA ? pA[i * a.in_sAxis] : (T)0;
+            z.y = okB ? pA[i * a.in_sAxis + a.in_offB] : (T)0;
+            buf[i * LD + c] = z;
+        }
+    }
+    __syncthreads();
+    E::forward(buf, red2, bc, tw, twstride, tw, c, g);
+
+    if (MODE == MODE_PLAIN) {
+        const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
+        T* qA = a.out + other * a.out_sOther + xA;
+        const T sc = (T)a.scale;
+        E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
+            if (okA) qA[i * a.out_sAxis] = v.x * sc;
+            if (okB) qA[i * a.out_sAxis + a.out_offB] = v.y * sc;
+        });
+        return;
+    }
+
+    {
+        const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
+        const long long base = other * a.in_sOther + xA;
+        const long long oB = a.in_offB;
+        const T invC = (T)a.invC;
+        E::post(buf, red, red2, bc, c, g, [&](int k, C Fv) {
+            const long long iA = base + k * a.in_sAxis, iB = iA + oB;
+            const T F[2] = {Fv.x, Fv.y};
+            T s[2] = {0, 0};
+            const bool ok[2] = {okA, okB};
+            const long long ix[2] = {iA, iB};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!ok[h]) continue;
+                const long long i = ix[h];
+                if (MODE == MODE_T0) {
+                    a.U[i] = F[h];
+                    s[h] = F[h];
+                } else if (MODE == MODE_TA || MODE == MODE_TB) {
+                    if (MODE == MODE_TA) a.F1[i] = F[h]; else a.F2[i] = F[h];
+                    const T Q = a.CQ[2 * i], ph = a.CQ[2 * i + 1];
+                    s[h] = Q * a.U[i] + ph * F[h];
+                } else if (MODE == MODE_TC) {
+                    a.F3[i] = F[h];
+                    const T Q = a.CQ[2 * i], ph = a.CQ[2 * i + 1];
+                    const T f1 = a.F1[i];
+                    const T ah = Q * a.U[i] + ph * f1;
+                    s[h] = Q * ah + ph * ((T)2 * F[h] - f1);
+                } else {  // MODE_TD
+                    const T R = a.CR[4 * i], p1 = a.CR[4 * i + 1], p2 = a.CR[4 * i + 2], p3 = a.CR[4 * i + 3];
+                    const T un = R * a.U[i] + p1 * a.F1[i] + p2 * (a.F2[i] + a.F3[i]) + p3 * F[h];
+                    a.U[i] = un;
+                    s[h] = un;
+                }
+            }
+            C z;
+            z.x = s[0] * invC;
+            z.y = s[1] * invC;
+            buf[k * LD + c] = z;
+        });
+    }
+    __syncthreads();
+    E::forward(buf, red2, bc, tw, twstride, tw, c, g);
+    {
+        const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
+        T* qA = a.out + other * a.out_sOther + xA;
+        E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
+            if (okA) qA[i * a.out_sAxis] = v.x;
+            if (okB) qA[i * a.out_sAxis + a.out_offB] = v.y;
+        });
+    }
+    if (MODE == MODE_TD && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) a.clock->k += 1;
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(kThreads) x2_kernel(const XArgs<T> a) {
+    constexpr int CC = TileOf<T, N>::CC;
+    using E = typename TileOf<T, N>::E;
+    using C = typename E::C;
+    constexpr int LD = E::LD, G = E::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* red = buf + E::ROWS * LD;
+    C* red2 = red + G * CC;
+    const int tid = threadIdx.x, c = tid % CC, g = tid / CC;
+    const AxisDev& ax = a.ax;
+    const int n = ax.n, bc = ax.bc;
+    const C* tw = static_cast<const C*>(ax.tw);
+    const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
+    const int shiftB = (a.S == 2) ? 0 : CC;
+    const int r0 = blockIdx.x * (a.S == 2 ? CC : 2 * CC);
+
+    // transposed load: a warp reads 32 consecutive x of one row
+#pragma unroll 1
+    for (int cc = 0; cc < CC; ++cc) {
+        const int rA = r0 + cc, rB = rA + shiftB;
+        const T* pA = a.in + (long long)rA * a.in_pitch;
+        for (int x = tid; x < n; x += kThreads) {
+            C z;
+            z.x = rA < a.rows ? pA[x] : (T)0;
+            z.y = rB < a.rows ? pA[a.in_offB + x] : (T)0;
+            buf[x * LD + cc] = z;
+        }
+    }
+    __syncthreads();
+    E::forward(buf, red2, bc, tw, twstride, tw, c, g);
+    if (MODE == MODE_REACT) {
+        const double t = a.clock->t0 + ((double)a.clock->k + a.stage_frac) * a.tau;
+        const int rA = r0 + c, rB = rA + shiftB;
+        E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
+            C f;
+            if (a.S == 2) {
+                react2<T>(a.re, v.x, v.y, f.x, f.y);
+            } else {
+                const double x = ax.lo + (ax.node0 + i) * ax.h;
+                const int yA = rA % a.ny, yB = rB % a.ny;
+                const double ya = a.ay.lo + (a.ay.node0 + yA) * a.ay.h;
+                const double yb = a.ay.lo + (a.ay.node0 + yB) * a.ay.h;
+                f.x = react1<T>(a.re, v.x, x, ya, t);
+                f.y = react1<T>(a.re, v.y, x, yb, t);
+            }
+            buf[i * LD + c] = f;
+        });
+        __syncthreads();
+        E::forward(buf, red2, bc, tw, twstride, tw, c, g);
+    }
+    E::post(buf, red, red2, bc, c, g, [&](int i, C v) { buf[i * LD + c] = v; });
+    __syncthreads();
+#pragma unroll 1
+    for (int cc = 0; cc < CC; ++cc) {
+        const int rA = r0 + cc, rB = rA + shiftB;
+        T* qA = a.out + (long long)rA * a.out_pitch;
+        for (int x = tid; x < a.out_fill || x < n; x += kThreads) {
+            const C v = x < n ? buf[x * LD + cc] : czero<C>();
+            if (rA < a.rows) qA[x] = v.x;
+            if (rB < a.rows) qA[a.out_offB + x] = v.y;
+        }
+    }
+}
+
+// ---- launch --------------------------------------------------------------------------
+
+template <typename T, int N>
+cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+    const size_t smem = TileOf<T, N>::E::smem_bytes();
+    void (*k)(const ColArgs<T>) = nullptr;
+    switch (mode) {
+        case MODE_PLAIN: k = col2_kernel<T, N, MODE_PLAIN>; break;
+        case MODE_T0: k = col2_kernel<T, N, MODE_T0>; break;
+        case MODE_TA: k = col2_kernel<T, N, MODE_TA>; break;
+        case MODE_TB: k = col2_kernel<T, N, MODE_TB>; break;
+        case MODE_TC: k = col2_kernel<T, N, MODE_TC>; break;
+        default: k = col2_kernel<T, N, MODE_TD>; break;
+    }
+    k<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t x2_launch(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+    const size_t smem = TileOf<T, N>::E::smem_bytes();
+    void (*k)(const XArgs<T>) = mode == MODE_REACT ? x2_kernel<T, N, MODE_REACT> : x2_kernel<T, N, MODE_PLAIN>;
+    k<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t prepare2() {
+    const int m = kMaxDynSmem2;
+    void (*ks[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_PLAIN>, col2_kernel<T, N, MODE_T0>,
+                                      col2_kernel<T, N, MODE_TA>,    col2_kernel<T, N, MODE_TB>,
+                                      col2_kernel<T, N, MODE_TC>,    col2_kernel<T, N, MODE_TD>};
+    for (auto k : ks) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        if (e != cudaSuccess) return e;
+    }
+    void (*xs[])(const XArgs<T>) = {x2_kernel<T, N, MODE_PLAIN>, x2_kernel<T, N, MODE_REACT>};
+    for (auto k : xs) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+#define SFRD_V2_INSTANTIATE(T, N)                                                                  \
+    template cudaError_t col2_launch<T, N>(const ColArgs<T>&, int, dim3, cudaStream_t);           \
+    template cudaError_t x2_launch<T, N>(const XArgs<T>&, int, dim3, cudaStream_t);               \
+    template cudaError_t prepare2<T, N>();
+
+}  // namespace v2
+}  // namespace sfrd

@@ -1,0 +1,71 @@
+// Pointwise reaction terms f(u, t) evaluated inside the contiguous-axis pass.
+#pragma once
+
+#include "sfrd_internal.h"
+
+namespace sfrd {
+
+// ---- reaction terms (Section 5.2; parameters as documented in sfrd.h) -----------
+
+template <typename T>
+__device__ __forceinline__ void react2(const ReactDev& re, T u, T v, T& fu, T& fv) {
+    switch (re.kind) {
+        case SFRD_REACT_FHN: {
+            const T mu = (T)re.p[0], eps = (T)re.p[1], beta = (T)re.p[2], gam = (T)re.p[3], del = (T)re.p[4];
+            fu = u * ((T)1 - u) * (u - mu) - v;
+            fv = eps * (beta * u - gam * v - del);
+        } break;
+        case SFRD_REACT_GRAY_SCOTT: {
+            const T F = (T)re.p[0], K = (T)re.p[1];
+            const T uvv = u * v * v;
+            fu = -uvv + F * ((T)1 - u);
+            fv = uvv - (F + K) * v;
+        } break;
+        case SFRD_REACT_SCHNAKENBERG: {
+            const T g = (T)re.p[0], a = (T)re.p[1], b = (T)re.p[2];
+            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
+            const T uuv = U * U * V;
+            fu = g * (a - U + uuv);
+            fv = g * (b - uuv);
+        } break;
+        case SFRD_REACT_GIERER_MEINHARDT: {
+            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
+            fu = (T)re.p[0] * U * U / V - (T)re.p[1] * U;
+            fv = (T)re.p[2] * U * U - (T)re.p[3] * V;
+        } break;
+        case SFRD_REACT_LINEAR:
+            fu = (T)re.p[0] * u;
+            fv = (T)re.p[0] * v;
+            break;
+        default:
+            fu = 0;
+            fv = 0;
+    }
+}
+
+// Single-species terms; x, y are node coordinates, t the stage time.
+template <typename T>
+__device__ __forceinline__ T react1(const ReactDev& re, T u, double x, double y, double t) {
+    switch (re.kind) {
+        case SFRD_REACT_LINEAR:
+            return (T)re.p[0] * u;
+        case SFRD_REACT_HUXLEY_MMS: {
+            // Example 2: exact solution t^alpha cos^3(2 pi x) cos^3(2 pi y); p = [alpha, k1..k4]
+            // with Phi = k1 c1x c1y + k2 c3x c1y + k3 c1x c3y + k4 c3x c3y, cNz = cos(2 N pi z).
+            const double al = re.p[0];
+            const double c1x = cospi(2.0 * x), c1y = cospi(2.0 * y);
+            const double c3x = cospi(6.0 * x), c3y = cospi(6.0 * y);
+            const double g = c1x * c1x * c1x * c1y * c1y * c1y;
+            const double Phi = re.p[1] * c1x * c1y + re.p[2] * c3x * c1y + re.p[3] * c1x * c3y + re.p[4] * c3x * c3y;
+            const double ta = t > 0 ? pow(t, al) : 0.0;
+            const double dta = t > 0 ? al * pow(t, al - 1.0) : 0.0;
+            const double w = ta * g;
+            const double src = dta * g + ta * Phi - w * (1.0 - w) * (w - 1.0);
+            return u * ((T)1 - u) * (u - (T)1) + (T)src;
+        }
+        default:
+            return 0;
+    }
+}
+
+}  // namespace sfrd

@@ -76,7 +76,7 @@ static bool factor(int M, std::vector<int>& r) {
     if (rem == 1 && k2 == 1) r.push_back(2);
     while (m % 3 == 0) { m /= 3; r.push_back(3); }
     while (m % 5 == 0) { m /= 5; r.push_back(5); }
-    return m == 1 && (int)r.size() <= kMaxStages;
+    return m == 1 && (int)r.size() <= kMaxStages;  // (M <= 2048: at most 4 stages of 8 plus small factors)
 }
 
 // Slot of extension index k after the in-place DIF with radices r[0..s-1]:
@@ -155,8 +155,12 @@ static int create(Plan** out, const sfrd_grid* g, int bc, const double* alpha, c
             p->lo[d] = g->lo[d];
             p->hi[d] = g->hi[d];
             p->n[d] = unknowns(bc, g->N[d]);
-            const long long M = bc == SFRD_BC_PERIODIC ? g->N[d] : 2 * g->N[d];
-            if (M > kMaxFFT || !factor((int)M, p->radix[d])) {
+            const long long N = g->N[d];
+            const long long M = bc == SFRD_BC_PERIODIC ? N : 2 * N;
+            // power-of-two lengths up to 1024 run on the register engine (its tables have length M);
+            // other lengths need a {2,3,5}-smooth M <= 1024 for the shared-memory engine
+            const bool pow2ok = N >= v2::kMinN && N <= v2::kMaxN && (N & (N - 1)) == 0;
+            if ((!pow2ok && M > kMaxFFT) || !factor((int)M, p->radix[d])) {
                 delete p;
                 return SFRD_EUNSUPPORTED;
             }
@@ -165,6 +169,15 @@ static int create(Plan** out, const sfrd_grid* g, int bc, const double* alpha, c
             p->Nint[d] = 1;
             p->n[d] = 1;
             p->M[d] = 1;
+        }
+    }
+    // register FFT engine for power-of-two lengths (SFRD_ENGINE=generic forces the shared-memory engine)
+    {
+        const char* eng = std::getenv("SFRD_ENGINE");
+        const bool generic = eng && std::strcmp(eng, "generic") == 0;
+        for (int d = 0; d < g->dim; ++d) {
+            const long long N = p->Nint[d];
+            p->v2[d] = !generic && N >= v2::kMinN && N <= v2::kMaxN && (N & (N - 1)) == 0;
         }
     }
     p->pitch = (p->n[0] + 3) / 4 * 4;

@@ -108,7 +108,8 @@ struct Plan {
     double alpha[2] = {0, 0}, kappa[2] = {0, 0};
     double dt = 0;
     ReactDev re{};
-    int CC = 16;               // complex columns per tile
+    int CC = 16;               // complex columns per tile (generic engine)
+    bool v2[3] = {false, false, false};   // axis uses the register FFT engine
     size_t esize = 8;
 
     // host tables (kept alive for async uploads)
@@ -142,6 +143,17 @@ template <typename T> cudaError_t launch_inverse(Plan& p, const void* uhat, void
 template <typename T> cudaError_t launch_coef_init(Plan& p, cudaStream_t s);
 template <typename T> cudaError_t launch_coef_copy(Plan& p, int which, void* out, cudaStream_t s);
 template <typename T> cudaError_t prepare_kernels(const Plan& p);
+
+// Register-FFT passes for power-of-two axis lengths (passes2.cuh, one translation unit per length).
+namespace v2 {
+constexpr int kMaxDynSmem2 = 227 * 1024;
+constexpr int kMinN = 64, kMaxN = 1024;
+// Columns per tile of the register engine (kept in sync with fft2.cuh's TileCC).
+constexpr int cc_for(bool f64, int N) { return f64 ? (N >= 1024 ? 4 : 8) : (N >= 1024 ? 8 : 16); }
+template <typename T, int N> cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s);
+template <typename T, int N> cudaError_t x2_launch(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s);
+template <typename T, int N> cudaError_t prepare2();
+}  // namespace v2
 cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s);
 
 int kernels_per_step(const Plan& p);

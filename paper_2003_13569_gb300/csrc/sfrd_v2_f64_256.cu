@@ -1,0 +1,8 @@
+// Register-FFT passes, F64, axis length 256.
+#include "passes2.cuh"
+
+namespace sfrd {
+namespace v2 {
+SFRD_V2_INSTANTIATE(double, 256)
+}  // namespace v2
+}  // namespace sfrd

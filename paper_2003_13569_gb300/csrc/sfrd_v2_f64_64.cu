@@ -1,0 +1,8 @@
+// Register-FFT passes, F64, axis length 64.
+#include "passes2.cuh"
+
+namespace sfrd {
+namespace v2 {
+SFRD_V2_INSTANTIATE(double, 64)
+}  // namespace v2
+}  // namespace sfrd

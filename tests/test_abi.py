@@ -82,7 +82,8 @@ def test_valid_plan_reports_sizes(sfrd):
     (dict(reaction=99), -1),
     (dict(reaction="fhn", alpha=(1.5,), kappa=(1.0,)), -1),     # FHN needs two species
     (dict(N=(14, 16, 1), bc="periodic"), -2),                   # 14 = 2 * 7 is not {2,3,5}-smooth
-    (dict(N=(1024, 16, 1), bc="neumann"), -2),                  # extension length 2048 > 1024
+    (dict(N=(2048, 16, 1), bc="neumann"), -2),                  # beyond both engines' lengths
+    (dict(N=(600, 16, 1), bc="neumann"), -2),                   # extension length 1200 > 1024, not a power of 2
     (dict(dim=1), -2),
 ])
 def test_invalid_arguments_are_rejected(sfrd, kw, code):
