@@ -251,10 +251,24 @@ struct Eng {
 
     // Z (natural) -> transform values; sink(i, value) is called for every unknown i
     // of this thread's output range after a barrier (so the sink may write V).
+    // Compensated (Kahan) accumulation s += d with running error e; used by the
+    // prefix sums of the odd-index outputs so that their rounding error does not
+    // grow with the number of terms.
+    static __device__ __forceinline__ void kadd(C& s, C& e, C d) {
+        C y, t;
+        y.x = d.x - e.x;
+        y.y = d.y - e.y;
+        t.x = s.x + y.x;
+        t.y = s.y + y.y;
+        e.x = (t.x - s.x) - y.x;
+        e.y = (t.y - s.y) - y.y;
+        s = t;
+    }
+
     template <class Sink>
     static __device__ __forceinline__ void post(C* buf, C* red, const C* red2, int bc, int c, int g, Sink&& sink) {
         C ev[CH], od[CH];   // even-index outputs, running odd-index partial sums
-        C run = czero<C>();
+        C run = czero<C>(), err = czero<C>();
         const int k0 = g * CH;
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
@@ -274,8 +288,8 @@ struct Eng {
                     ev[t] = Ik;
                     C d = Rk;
                     if (k == 0) { d.x *= (T)0.5; d.y *= (T)0.5; }
-                    run = cadd(run, d);
-                    od[t] = run;
+                    kadd(run, err, d);
+                    od[t] = csub(run, err);
                 } else {
                     ev[t] = Rk;
                     C d = Ik;
@@ -284,8 +298,8 @@ struct Eng {
 #pragma unroll 4
                         for (int q = 0; q < G; ++q) d = cadd(d, red2[q * CC + c]);
                     }
-                    run = cadd(run, d);
-                    od[t] = run;
+                    kadd(run, err, d);
+                    od[t] = csub(run, err);
                 }
             }
         }
@@ -294,11 +308,13 @@ struct Eng {
             const C zh = buf[H * LD + c];     // k = N/2: R = Re, I = 0 for both lines
             nyq = zh;
         }
-        if (bc != SFRD_BC_PERIODIC) red[g * CC + c] = run;
+        if (bc != SFRD_BC_PERIODIC) red[g * CC + c] = csub(run, err);
         __syncthreads();   // all reads of Z done: the buffer becomes V
         C pre_sum = czero<C>();
         if (bc != SFRD_BC_PERIODIC) {
-            for (int q = 0; q < g; ++q) pre_sum = cadd(pre_sum, red[q * CC + c]);
+            C perr = czero<C>();
+            for (int q = 0; q < g; ++q) kadd(pre_sum, perr, red[q * CC + c]);
+            pre_sum = csub(pre_sum, perr);
         }
 #pragma unroll
         for (int t = 0; t < CH; ++t) {

@@ -35,13 +35,21 @@ __global__ void __launch_bounds__(kThreads) col2_kernel(const ColArgs<T> a) {
     const long long other = blockIdx.y;
 
     {
+        // all loads of this thread issued before any shared-memory store
+        constexpr int NL = (E::ROWS + G - 1) / G;
         const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
         const T* pA = a.in + other * a.in_sOther + xA;
-        for (int i = g; i < n; i += G) {
-            C z;
-            z.x = okA ? pA[i * a.in_sAxis] : (T)0;
-            z.y = okB ? pA[i * a.in_sAxis + a.in_offB] : (T)0;
-            buf[i * LD + c] = z;
+        C z[NL];
+#pragma unroll
+        for (int t = 0; t < NL; ++t) {
+            const int i = g + t * G;
+            z[t].x = (okA && i < n) ? pA[i * a.in_sAxis] : (T)0;
+            z[t].y = (okB && i < n) ? pA[i * a.in_sAxis + a.in_offB] : (T)0;
+        }
+#pragma unroll
+        for (int t = 0; t < NL; ++t) {
+            const int i = g + t * G;
+            if (i < n) buf[i * LD + c] = z[t];
         }
     }
     __syncthreads();
@@ -130,16 +138,32 @@ __global__ void __launch_bounds__(kThreads) x2_kernel(const XArgs<T> a) {
     const int shiftB = (a.S == 2) ? 0 : CC;
     const int r0 = blockIdx.x * (a.S == 2 ? CC : 2 * CC);
 
-    // transposed load: a warp reads 32 consecutive x of one row
-#pragma unroll 1
-    for (int cc = 0; cc < CC; ++cc) {
-        const int rA = r0 + cc, rB = rA + shiftB;
-        const T* pA = a.in + (long long)rA * a.in_pitch;
-        for (int x = tid; x < n; x += kThreads) {
-            C z;
-            z.x = rA < a.rows ? pA[x] : (T)0;
-            z.y = rB < a.rows ? pA[a.in_offB + x] : (T)0;
-            buf[x * LD + cc] = z;
+    // transposed load: warp w reads rows w, w + 8, ... ; lane l reads x = l, l + 32, ...
+    {
+        constexpr int NW = kThreads / 32;               // warps
+        constexpr int RW = (CC + NW - 1) / NW;          // rows per warp
+        constexpr int XL = (E::ROWS + 31) / 32;         // x per lane
+        const int w = tid >> 5, l = tid & 31;
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr) {
+            const int cc = w + rr * NW;
+            const int rA = r0 + cc, rB = rA + shiftB;
+            const bool okA = cc < CC && rA < a.rows, okB = cc < CC && rB < a.rows;
+            const T* pA = a.in + (long long)rA * a.in_pitch;
+            C z[XL];
+#pragma unroll
+            for (int t = 0; t < XL; ++t) {
+                const int x = l + 32 * t;
+                z[t].x = (okA && x < n) ? pA[x] : (T)0;
+                z[t].y = (okB && x < n) ? pA[a.in_offB + x] : (T)0;
+            }
+            if (cc < CC) {
+#pragma unroll
+                for (int t = 0; t < XL; ++t) {
+                    const int x = l + 32 * t;
+                    if (x < n) buf[x * LD + cc] = z[t];
+                }
+            }
         }
     }
     __syncthreads();
@@ -166,14 +190,22 @@ __global__ void __launch_bounds__(kThreads) x2_kernel(const XArgs<T> a) {
     }
     E::post(buf, red, red2, bc, c, g, [&](int i, C v) { buf[i * LD + c] = v; });
     __syncthreads();
-#pragma unroll 1
-    for (int cc = 0; cc < CC; ++cc) {
-        const int rA = r0 + cc, rB = rA + shiftB;
-        T* qA = a.out + (long long)rA * a.out_pitch;
-        for (int x = tid; x < a.out_fill || x < n; x += kThreads) {
-            const C v = x < n ? buf[x * LD + cc] : czero<C>();
-            if (rA < a.rows) qA[x] = v.x;
-            if (rB < a.rows) qA[a.out_offB + x] = v.y;
+    {
+        constexpr int NW = kThreads / 32;
+        constexpr int RW = (CC + NW - 1) / NW;
+        const int w = tid >> 5, l = tid & 31;
+        const int xend = a.out_fill > n ? a.out_fill : n;
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr) {
+            const int cc = w + rr * NW;
+            if (cc >= CC) continue;
+            const int rA = r0 + cc, rB = rA + shiftB;
+            T* qA = a.out + (long long)rA * a.out_pitch;
+            for (int x = l; x < xend; x += 32) {
+                const C v = x < n ? buf[x * LD + cc] : czero<C>();
+                if (rA < a.rows) qA[x] = v.x;
+                if (rB < a.rows) qA[a.out_offB + x] = v.y;
+            }
         }
     }
 }
