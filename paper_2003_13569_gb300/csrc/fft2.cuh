@@ -174,14 +174,13 @@ struct Eng {
     static constexpr int ROWS = N + 1;              // buffer rows (n <= N + 1)
 
     static constexpr size_t smem_bytes() {
-        return (size_t)ROWS * LD * sizeof(C) + (size_t)2 * G * CC * sizeof(C);
+        return (size_t)ROWS * LD * sizeof(C) + (size_t)2 * G * CC * sizeof(C) + (size_t)2 * N * sizeof(C);
     }
 
     // Pre-processed input z_j of the packed DFT, read from the value buffer.
-    static __device__ __forceinline__ C pre(const C* V, int bc, int j, int c, const C* __restrict__ tw2,
-                                            C& anchor) {
+    static __device__ __forceinline__ C pre(const C* V, int bc, int j, int c, const C* tws, C& anchor) {
         if (bc == SFRD_BC_PERIODIC) return V[j * LD + c];
-        const C w = __ldg(tw2 + j);       // (cos(j pi/N), -sin(j pi/N))
+        const C w = tws[j];               // (cos(j pi/N), -sin(j pi/N))
         const T s = -w.y;
         if (bc == SFRD_BC_DIRICHLET) {
             if (j == 0) return czero<C>();
@@ -208,8 +207,9 @@ struct Eng {
     // V (natural, unknown index) -> pre-processing -> DFT_N -> Z (natural order).
     // Entry: V complete (after a barrier).  Exit: Z complete (after a barrier).
     // red2[g][c] receives this thread's part of the Neumann anchor.
-    static __device__ __forceinline__ void forward(C* buf, C* red2, int bc, const C* __restrict__ twN, int twstride,
-                                                   const C* __restrict__ tw2, int c, int g) {
+    // tws: the axis table in shared memory, omega_{N*twstride}^m (twstride = 1 periodic, 2 otherwise).
+    static __device__ __forceinline__ void forward(C* buf, C* red2, int bc, const C* tws, int twstride, int c,
+                                                   int g) {
         C a[NO1][R1];
         C anchor = czero<C>();
 #pragma unroll
@@ -217,10 +217,10 @@ struct Eng {
             const int n2 = g + o * G;
             if (R2 % G == 0 || n2 < R2) {
 #pragma unroll
-                for (int n1 = 0; n1 < R1; ++n1) a[o][n1] = pre(buf, bc, R2 * n1 + n2, c, tw2, anchor);
+                for (int n1 = 0; n1 < R1; ++n1) a[o][n1] = pre(buf, bc, R2 * n1 + n2, c, tws, anchor);
                 RDft<R1, C>::run(a[o]);
 #pragma unroll
-                for (int k1 = 1; k1 < R1; ++k1) a[o][k1] = cmul(a[o][k1], __ldg(twN + (n2 * k1) * twstride));
+                for (int k1 = 1; k1 < R1; ++k1) a[o][k1] = cmul(a[o][k1], tws[(n2 * k1) * twstride]);
             }
         }
         red2[g * CC + c] = anchor;

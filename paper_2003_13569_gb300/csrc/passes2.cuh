@@ -17,7 +17,7 @@ struct TileOf {
 };
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kThreads) col2_kernel(const ColArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, 3) col2_kernel(const ColArgs<T> a) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N>::E;
     using C = typename E::C;
@@ -26,11 +26,13 @@ __global__ void __launch_bounds__(kThreads) col2_kernel(const ColArgs<T> a) {
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* red = buf + E::ROWS * LD;
     C* red2 = red + G * CC;
+    C* tws = red2 + G * CC;
     const int tid = threadIdx.x, c = tid % CC, g = tid / CC;
     const AxisDev& ax = a.ax;
     const int n = ax.n, bc = ax.bc;
     const C* tw = static_cast<const C*>(ax.tw);
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
+    for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);   // visible after the first barrier
     const int xA = blockIdx.x * a.xw + c, xB = xA + a.bshift;
     const long long other = blockIdx.y;
 
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(kThreads) col2_kernel(const ColArgs<T> a) {
         }
     }
     __syncthreads();
-    E::forward(buf, red2, bc, tw, twstride, tw, c, g);
+    E::forward(buf, red2, bc, tws, twstride, c, g);
 
     if (MODE == MODE_PLAIN) {
         const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) col2_kernel(const ColArgs<T> a) {
         });
     }
     __syncthreads();
-    E::forward(buf, red2, bc, tw, twstride, tw, c, g);
+    E::forward(buf, red2, bc, tws, twstride, c, g);
     {
         const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
         T* qA = a.out + other * a.out_sOther + xA;
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) col2_kernel(const ColArgs<T> a) {
 }
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kThreads) x2_kernel(const XArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, 3) x2_kernel(const XArgs<T> a) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N>::E;
     using C = typename E::C;
@@ -130,11 +132,13 @@ __global__ void __launch_bounds__(kThreads) x2_kernel(const XArgs<T> a) {
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* red = buf + E::ROWS * LD;
     C* red2 = red + G * CC;
+    C* tws = red2 + G * CC;
     const int tid = threadIdx.x, c = tid % CC, g = tid / CC;
     const AxisDev& ax = a.ax;
     const int n = ax.n, bc = ax.bc;
     const C* tw = static_cast<const C*>(ax.tw);
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
+    for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);   // visible after the first barrier
     const int shiftB = (a.S == 2) ? 0 : CC;
     const int r0 = blockIdx.x * (a.S == 2 ? CC : 2 * CC);
 
@@ -167,11 +171,16 @@ __global__ void __launch_bounds__(kThreads) x2_kernel(const XArgs<T> a) {
         }
     }
     __syncthreads();
-    E::forward(buf, red2, bc, tw, twstride, tw, c, g);
+    E::forward(buf, red2, bc, tws, twstride, c, g);
     if (MODE == MODE_REACT) {
+        E::post(buf, red, red2, bc, c, g, [&](int i, C v) { buf[i * LD + c] = v; });
+        __syncthreads();
+        // pointwise reaction on the physical values (kept out of the unrolled code)
         const double t = a.clock->t0 + ((double)a.clock->k + a.stage_frac) * a.tau;
         const int rA = r0 + c, rB = rA + shiftB;
-        E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
+#pragma unroll 1
+        for (int i = g; i < n; i += G) {
+            const C v = buf[i * LD + c];
             C f;
             if (a.S == 2) {
                 react2<T>(a.re, v.x, v.y, f.x, f.y);
@@ -184,9 +193,9 @@ __global__ void __launch_bounds__(kThreads) x2_kernel(const XArgs<T> a) {
                 f.y = react1<T>(a.re, v.y, x, yb, t);
             }
             buf[i * LD + c] = f;
-        });
+        }
         __syncthreads();
-        E::forward(buf, red2, bc, tw, twstride, tw, c, g);
+        E::forward(buf, red2, bc, tws, twstride, c, g);
     }
     E::post(buf, red, red2, bc, c, g, [&](int i, C v) { buf[i * LD + c] = v; });
     __syncthreads();

@@ -99,9 +99,13 @@ def test_forward_transform_register_engine(dim, N, bc, dtype, S):
     s = sf.Solver(cfg, dtype=dtype)
     u = _rand_fields(cfg, seed=11)
     got = _np(s.forward(u))
-    tol = 1e-12 if dtype == "f64" else 4e-6
+    # FP32: the odd-index sine/cosine outputs are running sums of DFT values, whose rounding
+    # errors add up like a random walk over N/2 terms (max-norm ~ sqrt(N) eps per axis).
+    tol = 1e-12 if dtype == "f64" else (4e-6 if bc == "periodic" else 3e-5)
     for sp in range(S):
         assert rel_max(got[sp], library_forward(u[sp], bc, N)) < tol
+        if dtype == "f32":
+            assert rel_l2(got[sp], library_forward(u[sp], bc, N)) < 3e-6
     back = _np(s.inverse(got))
     for sp in range(S):
         assert rel_max(back[sp], u[sp]) < tol
