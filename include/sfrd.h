@@ -190,6 +190,36 @@ int sfrd_coefficients(sfrd_plan_t plan, int32_t which, void* out);
  * Errors: SFRD_ESTATE before sfrd_load. */
 int sfrd_profile_step(sfrd_plan_t plan, int32_t cap, float* ms, int32_t* kind);
 
+/* ---- discrete adjoint (gradients through nsteps steps) ---------------------
+ * Available when every axis length N is a power of two in [64, 1024]
+ * (SFRD_EUNSUPPORTED otherwise).  The adjoint is the exact transpose of the
+ * library's own FP arithmetic path (transposed transforms, the same
+ * coefficient arrays, the reaction Jacobian transposed), i.e. the gradient of
+ * the discrete map u0 -> u(t0 + nsteps tau) of Eq. ETDRK4P13.
+ *
+ * Memory: a caller-owned device buffer of sfrd_adjoint_workspace_bytes(nsteps,
+ * ckpt_every) bytes (256-byte aligned) holds one spectral checkpoint every
+ * ckpt_every steps and, during the reverse sweep, the stage intermediates of
+ * one segment of ckpt_every steps (recomputed from its checkpoint). */
+int sfrd_adjoint_workspace_bytes(sfrd_plan_t plan, int64_t nsteps, int64_t ckpt_every, size_t* bytes);
+
+/* u <- u(t0 + nsteps tau) like sfrd_run, also writing the checkpoints that
+ * sfrd_adjoint needs into adj_ws.  u is a device field, overwritten. */
+int sfrd_run_checkpointed(sfrd_plan_t plan, void* u, double t0, int64_t nsteps, int64_t ckpt_every,
+                          void* adj_ws, size_t adj_bytes);
+
+/* Gradients of a loss l(u_T), u_T = u(t0 + nsteps tau), after sfrd_run_checkpointed
+ * with the same (t0, nsteps, ckpt_every, adj_ws):
+ *   dLduT  (device, [S][...], read)  : dl/du_T
+ *   dLdu0  (device, [S][...], write) : dl/du0
+ *   dLdalpha, dLdkappa (host, [S])   : dl/dalpha_s, dl/dkappa_s (NULL to skip)
+ *   dLdparams (host, [8])            : dl/dp of the reaction parameters p[0..4]
+ *                                      (p[5..7] reported as 0; NULL to skip).
+ * Synchronises the stream.  Leaves no resident state (call sfrd_load before
+ * sfrd_advance again). */
+int sfrd_adjoint(sfrd_plan_t plan, double t0, int64_t nsteps, int64_t ckpt_every, void* adj_ws, size_t adj_bytes,
+                 const void* dLduT, void* dLdu0, double* dLdalpha, double* dLdkappa, double* dLdparams);
+
 /* Release the plan and its CUDA graph (not the workspace). */
 void sfrd_destroy(sfrd_plan_t plan);
 

@@ -31,7 +31,8 @@ REACTION = {"none": 0, "linear": 1, "fhn": 2, "gray_scott": 3, "schnakenberg": 4
 COEFFICIENTS = ("R13", "Q13", "phi", "phi1", "phi2", "phi3")
 EXPORTS = ("sfrd_plan", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
            "sfrd_store", "sfrd_run", "sfrd_step", "sfrd_run_host", "sfrd_forward", "sfrd_inverse",
-           "sfrd_coefficients", "sfrd_profile_step", "sfrd_destroy", "sfrd_strerror", "sfrd_last_error")
+           "sfrd_coefficients", "sfrd_profile_step", "sfrd_adjoint_workspace_bytes", "sfrd_run_checkpointed",
+           "sfrd_adjoint", "sfrd_destroy", "sfrd_strerror", "sfrd_last_error")
 
 
 class Grid(ctypes.Structure):
@@ -69,6 +70,10 @@ _lib.sfrd_inverse.argtypes = [_P, _P, _P]
 _lib.sfrd_coefficients.argtypes = [_P, ctypes.c_int32, _P]
 _lib.sfrd_profile_step.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_int32)]
+_lib.sfrd_adjoint_workspace_bytes.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+_lib.sfrd_run_checkpointed.argtypes = [_P, _P, _D, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_size_t]
+_lib.sfrd_adjoint.argtypes = [_P, _D, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_size_t, _P, _P,
+                              ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)]
 _lib.sfrd_destroy.argtypes = [_P]
 _lib.sfrd_destroy.restype = None
 _lib.sfrd_strerror.argtypes = [ctypes.c_int]
@@ -241,6 +246,38 @@ class Solver:
         _check(_lib.sfrd_profile_step(self.handle, n, ms, kd), "sfrd_profile_step")
         return [(int(kd[i]), float(ms[i])) for i in range(n)]
 
+    # -- discrete adjoint ----------------------------------------------------
+    def _adj_ws(self, nsteps, K):
+        nb = ctypes.c_size_t()
+        _check(_lib.sfrd_adjoint_workspace_bytes(self.handle, int(nsteps), int(K), ctypes.byref(nb)),
+               "sfrd_adjoint_workspace_bytes")
+        key = (int(nsteps), int(K))
+        if getattr(self, "_adj_key", None) != key:
+            self._adj_buf = self.torch.empty(int(nb.value) + 256, dtype=self.torch.uint8, device=self.device)
+            self._adj_key = key
+        base = self._adj_buf.data_ptr()
+        return (base + 255) // 256 * 256, int(nb.value)
+
+    def run_checkpointed(self, u0, t0=0.0, nsteps=1, ckpt_every=50):
+        """u(t0 + nsteps dt), keeping the checkpoints that adjoint() needs."""
+        w = self._field(u0).clone()
+        ptr, nb = self._adj_ws(nsteps, ckpt_every)
+        _check(_lib.sfrd_run_checkpointed(self.handle, _ptr(w), float(t0), int(nsteps), int(ckpt_every),
+                                          ctypes.c_void_p(ptr), nb), "sfrd_run_checkpointed")
+        return w
+
+    def adjoint(self, dLduT, t0=0.0, nsteps=1, ckpt_every=50):
+        """(dL/du0, dL/dalpha[S], dL/dkappa[S], dL/dparams[8]) after run_checkpointed(u0, t0, nsteps, ckpt_every)."""
+        g = self._field(dLduT)
+        out = self.empty()
+        ptr, nb = self._adj_ws(nsteps, ckpt_every)
+        da = (ctypes.c_double * 2)()
+        dk = (ctypes.c_double * 2)()
+        dp = (ctypes.c_double * 8)()
+        _check(_lib.sfrd_adjoint(self.handle, float(t0), int(nsteps), int(ckpt_every), ctypes.c_void_p(ptr), nb,
+                                 _ptr(g), _ptr(out), da, dk, dp), "sfrd_adjoint")
+        return out, list(da)[:self.S], list(dk)[:self.S], list(dp)
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.sfrd_destroy(self.handle)
@@ -251,3 +288,58 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---- autograd ----------------------------------------------------------------------
+
+def _with_params(cfg, alpha, kappa, params):
+    c = dict(cfg)
+    c["alpha"] = tuple(float(x) for x in alpha)
+    c["kappa"] = tuple(float(x) for x in kappa)
+    r = dict(cfg["reaction"])
+    p = list(r.get("p", []))
+    for i, v in enumerate(params):
+        p[i] = float(v)
+    r["p"] = p
+    c["reaction"] = r
+    return c
+
+
+def _make_function():
+    import torch
+
+    class SfrdRun(torch.autograd.Function):
+        """u_T = ETDRK4-P13^nsteps(u0; alpha, kappa, reaction params), differentiated by the
+        library's discrete adjoint with checkpoints every ckpt_every steps."""
+
+        @staticmethod
+        def forward(ctx, u0, alpha, kappa, params, cfg, dtype, nsteps, ckpt_every, t0):
+            c = _with_params(cfg, alpha.detach().cpu().tolist(), kappa.detach().cpu().tolist(),
+                             params.detach().cpu().tolist())
+            s = Solver(c, dtype=dtype, device=u0.device)
+            uT = s.run_checkpointed(u0.detach(), t0=t0, nsteps=nsteps, ckpt_every=ckpt_every)
+            ctx.solver, ctx.meta = s, (t0, nsteps, ckpt_every, len(params))
+            return uT.to(u0.dtype)
+
+        @staticmethod
+        def backward(ctx, g):
+            t0, nsteps, K, npar = ctx.meta
+            du0, da, dk, dp = ctx.solver.adjoint(g.contiguous(), t0=t0, nsteps=nsteps, ckpt_every=K)
+            f64 = torch.float64
+            return (du0.to(g.dtype), torch.tensor(da, dtype=f64), torch.tensor(dk, dtype=f64),
+                    torch.tensor(dp[:npar], dtype=f64), None, None, None, None, None)
+
+    return SfrdRun
+
+
+_SFRD_RUN = None
+
+
+def run(u0, alpha, kappa, params, cfg, nsteps, ckpt_every=50, dtype=None, t0=0.0):
+    """Differentiable run: u0 [S][...] device tensor; alpha, kappa [S] and params (the reaction
+    parameter vector, in the order documented in sfrd.h) as float64 CPU tensors."""
+    global _SFRD_RUN
+    if _SFRD_RUN is None:
+        _SFRD_RUN = _make_function()
+    return _SFRD_RUN.apply(u0, alpha, kappa, params, cfg, dtype or cfg["dtype"], int(nsteps), int(ckpt_every),
+                           float(t0))

@@ -399,11 +399,11 @@ cudaError_t prepare_kernels(const Plan& p) {
     for (int d = 0; d < p.dim; ++d) {
         if (!p.v2[d]) continue;
         switch (p.Nint[d]) {
-            case 64: SFRD_TRY((v2::prepare2<T, 64>())); break;
-            case 128: SFRD_TRY((v2::prepare2<T, 128>())); break;
-            case 256: SFRD_TRY((v2::prepare2<T, 256>())); break;
-            case 512: SFRD_TRY((v2::prepare2<T, 512>())); break;
-            default: SFRD_TRY((v2::prepare2<T, 1024>())); break;
+            case 64: SFRD_TRY((v2::prepare2<T, 64>())); SFRD_TRY((v2::prepare_adj<T, 64>())); break;
+            case 128: SFRD_TRY((v2::prepare2<T, 128>())); SFRD_TRY((v2::prepare_adj<T, 128>())); break;
+            case 256: SFRD_TRY((v2::prepare2<T, 256>())); SFRD_TRY((v2::prepare_adj<T, 256>())); break;
+            case 512: SFRD_TRY((v2::prepare2<T, 512>())); SFRD_TRY((v2::prepare_adj<T, 512>())); break;
+            default: SFRD_TRY((v2::prepare2<T, 1024>())); SFRD_TRY((v2::prepare_adj<T, 1024>())); break;
         }
     }
     SFRD_TRY((prepare_cc<T, CCs<T>::a>()));
@@ -434,8 +434,7 @@ static Arr<T> dense_arr(const Plan& p, const void* ptr) {
 
 // Strided pass along axis d (1 = y, 2 = z) from array `in` to `out`.
 template <typename T>
-static cudaError_t run_col(const Plan& p, int d, int mode, const Arr<T>& in, const Arr<T>& out, double scale,
-                           cudaStream_t s) {
+static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>& out, double scale, dim3& grid) {
     ColArgs<T> a{};
     const int ny = p.n[1];
     a.in = in.ptr;
@@ -481,23 +480,50 @@ static cudaError_t run_col(const Plan& p, int d, int mode, const Arr<T>& in, con
     a.CR = wsT<T>(p, p.off_CR);
     a.clock = reinterpret_cast<Clock*>(p.ws + p.off_clock);
     a.ax = axis_dev<T>(p, d);
-    const int xlim = in.xlim > out.xlim ? in.xlim : out.xlim;
-    dim3 grid((xlim + a.xw - 1) / a.xw, gy, 1);
-    if (use2) {
-        switch (p.Nint[d]) {
-            case 64: return v2::col2_launch<T, 64>(a, mode, grid, s);
-            case 128: return v2::col2_launch<T, 128>(a, mode, grid, s);
-            case 256: return v2::col2_launch<T, 256>(a, mode, grid, s);
-            case 512: return v2::col2_launch<T, 512>(a, mode, grid, s);
-            default: return v2::col2_launch<T, 1024>(a, mode, grid, s);
-        }
+    a.dim = p.dim;
+    a.S = p.S;
+    for (int k = 0; k < 3; ++k) {
+        a.lam[k] = reinterpret_cast<const double*>(p.ws + p.off_lam[k]);
+        a.nk[k] = p.n[k];
     }
-    return dispatch_col<T>(p, a, mode, grid, tile_smem<T>(p, d), s);
+    for (int k = 0; k < 2; ++k) {
+        a.alpha[k] = p.alpha[p.S == 2 ? k : 0];
+        a.kappa[k] = p.kappa[p.S == 2 ? k : 0];
+    }
+    a.tau = p.dt;
+    const int xlim = in.xlim > out.xlim ? in.xlim : out.xlim;
+    grid = dim3((xlim + a.xw - 1) / a.xw, gy, 1);
+    return a;
 }
 
 template <typename T>
-static cudaError_t run_x(const Plan& p, int mode, const Arr<T>& in, const Arr<T>& out, int out_fill,
-                         double stage_frac, cudaStream_t s) {
+static cudaError_t launch_col(const Plan& p, int d, int mode, const ColArgs<T>& a, dim3 grid, cudaStream_t s) {
+    if (p.v2[d]) {
+        const bool adj = mode >= MODE_ADJ_ENTRY;
+        switch (p.Nint[d]) {
+            case 64: return adj ? v2::adj_col_launch<T, 64>(a, mode, grid, s) : v2::col2_launch<T, 64>(a, mode, grid, s);
+            case 128: return adj ? v2::adj_col_launch<T, 128>(a, mode, grid, s) : v2::col2_launch<T, 128>(a, mode, grid, s);
+            case 256: return adj ? v2::adj_col_launch<T, 256>(a, mode, grid, s) : v2::col2_launch<T, 256>(a, mode, grid, s);
+            case 512: return adj ? v2::adj_col_launch<T, 512>(a, mode, grid, s) : v2::col2_launch<T, 512>(a, mode, grid, s);
+            default: return adj ? v2::adj_col_launch<T, 1024>(a, mode, grid, s) : v2::col2_launch<T, 1024>(a, mode, grid, s);
+        }
+    }
+    if (mode >= MODE_ADJ_ENTRY) return cudaErrorNotSupported;
+    return dispatch_col<T>(p, a, mode, grid, tile_smem<T>(p, d), s);
+}
+
+// Strided pass along axis d (1 = y, 2 = z) from array `in` to `out`.
+template <typename T>
+static cudaError_t run_col(const Plan& p, int d, int mode, const Arr<T>& in, const Arr<T>& out, double scale,
+                           cudaStream_t s) {
+    dim3 grid;
+    const ColArgs<T> a = col_args<T>(p, d, in, out, scale, grid);
+    return launch_col<T>(p, d, mode, a, grid, s);
+}
+
+template <typename T>
+static XArgs<T> x_args(const Plan& p, const Arr<T>& in, const Arr<T>& out, int out_fill, double stage_frac,
+                       dim3& grid) {
     XArgs<T> a{};
     a.in = in.ptr;
     a.out = const_cast<T*>(out.ptr);
@@ -512,6 +538,7 @@ static cudaError_t run_x(const Plan& p, int mode, const Arr<T>& in, const Arr<T>
     a.rows = p.n[1] * p.n[2];
     a.out_fill = out_fill;
     a.ny = p.n[1];
+    a.nz = p.n[2];
     a.tau = p.dt;
     a.stage_frac = stage_frac;
     a.clock = reinterpret_cast<const Clock*>(p.ws + p.off_clock);
@@ -520,23 +547,41 @@ static cudaError_t run_x(const Plan& p, int mode, const Arr<T>& in, const Arr<T>
     if (p.dim == 3) a.az = axis_dev<T>(p, 2);
     a.re = p.re;
     const int per = two ? cc : 2 * cc;
-    dim3 grid((a.rows + per - 1) / per, 1, 1);
-    if (use2) {
+    grid = dim3((a.rows + per - 1) / per, 1, 1);
+    return a;
+}
+
+template <typename T>
+static cudaError_t launch_x(const Plan& p, int mode, const XArgs<T>& a, dim3 grid, cudaStream_t s) {
+    if (p.v2[0]) {
+        const bool adj = mode == MODE_XADJ;
         switch (p.Nint[0]) {
-            case 64: return v2::x2_launch<T, 64>(a, mode, grid, s);
-            case 128: return v2::x2_launch<T, 128>(a, mode, grid, s);
-            case 256: return v2::x2_launch<T, 256>(a, mode, grid, s);
-            case 512: return v2::x2_launch<T, 512>(a, mode, grid, s);
-            default: return v2::x2_launch<T, 1024>(a, mode, grid, s);
+            case 64: return adj ? v2::adj_x_launch<T, 64>(a, grid, s) : v2::x2_launch<T, 64>(a, mode, grid, s);
+            case 128: return adj ? v2::adj_x_launch<T, 128>(a, grid, s) : v2::x2_launch<T, 128>(a, mode, grid, s);
+            case 256: return adj ? v2::adj_x_launch<T, 256>(a, grid, s) : v2::x2_launch<T, 256>(a, mode, grid, s);
+            case 512: return adj ? v2::adj_x_launch<T, 512>(a, grid, s) : v2::x2_launch<T, 512>(a, mode, grid, s);
+            default: return adj ? v2::adj_x_launch<T, 1024>(a, grid, s) : v2::x2_launch<T, 1024>(a, mode, grid, s);
         }
     }
+    if (mode == MODE_XADJ) return cudaErrorNotSupported;
     return dispatch_x<T>(p, a, mode, grid, tile_smem<T>(p, 0), s);
 }
 
-// One step.  With `ev` non-null, event ev[i] is recorded before launch i and
-// ev[i+1] after it, and kind[i] receives the pass kind (PassKind).
 template <typename T>
-static cudaError_t step_impl(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind, int cap) {
+static cudaError_t run_x(const Plan& p, int mode, const Arr<T>& in, const Arr<T>& out, int out_fill,
+                         double stage_frac, cudaStream_t s) {
+    dim3 grid;
+    const XArgs<T> a = x_args<T>(p, in, out, out_fill, stage_frac, grid);
+    return launch_x<T>(p, mode, a, grid, s);
+}
+
+// One step.  With `ev` non-null, event ev[i] is recorded before launch i and
+// ev[i+1] after it, and kind[i] receives the pass kind (PassKind).  With `sv`
+// non-null the stage spectra and physical stage values are written to the
+// arrays it names (checkpointed recomputation for the adjoint).
+template <typename T>
+static cudaError_t step_impl(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind, int cap,
+                             const StepSave* sv = nullptr) {
     const Arr<T> W = internal_arr<T>(p, p.off_W);
     const int slow = p.dim == 3 ? 2 : 1;
     static const double frac[4] = {0.0, 0.5, 0.5, 1.0};
@@ -559,7 +604,12 @@ static cudaError_t step_impl(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind
             SFRD_TRY(done());
         }
         SFRD_TRY(mark(PASS_X));
-        SFRD_TRY(run_x<T>(p, MODE_REACT, W, W, p.pitch, frac[st], s));
+        {
+            dim3 grid;
+            XArgs<T> a = x_args<T>(p, W, W, p.pitch, frac[st], grid);
+            if (sv) a.save = static_cast<T*>(sv->stage[st]);
+            SFRD_TRY(launch_x<T>(p, MODE_REACT, a, grid, s));
+        }
         SFRD_TRY(done());
         if (p.dim == 3) {
             SFRD_TRY(mark(PASS_MID));
@@ -567,7 +617,17 @@ static cudaError_t step_impl(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind
             SFRD_TRY(done());
         }
         SFRD_TRY(mark(PASS_SLOW_A + st));
-        SFRD_TRY(run_col<T>(p, slow, MODE_TA + st, W, W, 1.0, s));
+        {
+            dim3 grid;
+            ColArgs<T> a = col_args<T>(p, slow, W, W, 1.0, grid);
+            if (sv) {
+                a.F1 = static_cast<T*>(sv->F[0]);
+                a.F2 = static_cast<T*>(sv->F[1]);
+                a.F3 = static_cast<T*>(sv->F[2]);
+                a.F4 = static_cast<T*>(sv->F[3]);
+            }
+            SFRD_TRY(launch_col<T>(p, slow, MODE_TA + st, a, grid, s));
+        }
         SFRD_TRY(done());
     }
     return cudaSuccess;
@@ -643,6 +703,146 @@ cudaError_t launch_coef_copy(Plan& p, int which, void* out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---- checkpointed forward and discrete adjoint (register engine) ----------------------
+
+// out = in * w (mul) or in / w (div) with w the product of the Neumann endpoint weights
+// (1/2 at nodes 0 and N of each axis) of a dense [S][n_z][n_y][n_x] field.
+template <typename T>
+__global__ void endpoint_weight_kernel(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nz, int S,
+                                       int divide) {
+    const long long total = (long long)S * nz * ny * nx;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % nx);
+        const long long r = idx / nx;
+        const int y = (int)(r % ny);
+        const int z = (int)((r / ny) % nz);
+        double w = 1.0;
+        if (nx > 1 && (x == 0 || x == nx - 1)) w *= 0.5;
+        if (ny > 1 && (y == 0 || y == ny - 1)) w *= 0.5;
+        if (nz > 1 && (z == 0 || z == nz - 1)) w *= 0.5;
+        out[idx] = divide ? (T)(in[idx] / w) : (T)(in[idx] * w);
+    }
+}
+
+template <typename T>
+static cudaError_t dense_weights(const Plan& p, const void* in, void* out, bool divide, cudaStream_t s) {
+    if (p.bc != SFRD_BC_NEUMANN) {
+        if (in != out) return cudaMemcpyAsync(out, in, (size_t)p.S * p.dense * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        return cudaSuccess;
+    }
+    endpoint_weight_kernel<T><<<512, 256, 0, s>>>(static_cast<const T*>(in), static_cast<T*>(out), p.n[0], p.n[1],
+                                                  p.n[2], p.S, divide ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_run_checkpointed(Plan& p, void* u, double t0, int64_t nsteps, int64_t K, char* aws,
+                                    const AdjLayout& L, cudaStream_t s) {
+    SFRD_TRY(launch_set_clock(p, t0, s, 0));
+    SFRD_TRY(launch_load<T>(p, u, s));
+    for (int64_t seg = 0; seg < L.nseg; ++seg) {
+        SFRD_TRY(cudaMemcpyAsync(aws + L.off_ckpt + seg * L.fld, p.ws + p.off_U, L.fld, cudaMemcpyDeviceToDevice, s));
+        const int64_t ns = (seg + 1) * K <= nsteps ? K : nsteps - seg * K;
+        for (int64_t j = 0; j < ns; ++j) SFRD_TRY(launch_step<T>(p, s));
+    }
+    return launch_store<T>(p, u, s);
+}
+
+template <typename T>
+cudaError_t launch_adjoint(Plan& p, double t0, int64_t nsteps, int64_t K, char* aws, const AdjLayout& L,
+                           const void* dLduT, void* dLdu0, cudaStream_t s) {
+    const Arr<T> W = internal_arr<T>(p, p.off_W);
+    const Arr<T> W2 = internal_arr<T>(p, p.off_W2);
+    const int slow = p.dim == 3 ? 2 : 1;
+    double C = 1.0;
+    for (int k = 0; k < p.dim; ++k) C *= (p.bc == SFRD_BC_PERIODIC) ? (double)p.Nint[k] : 0.5 * (double)p.Nint[k];
+    T* ub = reinterpret_cast<T*>(aws + L.off_Ub);
+    T* cb = reinterpret_cast<T*>(aws + L.off_Cb);
+    T* bb = reinterpret_cast<T*>(aws + L.off_Bb);
+    T* ab = reinterpret_cast<T*>(aws + L.off_Ab);
+    double* grad = reinterpret_cast<double*>(aws + L.off_grad);
+    const Arr<T> UB{ub, p.pitch, p.plane, p.pitch};
+    const Arr<T> D = dense_arr<T>(p, p.ws + p.off_D);
+    SFRD_TRY(cudaMemsetAsync(grad, 0, 16 * sizeof(double), s));
+    SFRD_TRY(cudaMemsetAsync(aws + L.off_Ub, 0, 4 * L.fld, s));
+
+    // entry: Ub~ = T(g ./ w) / C
+    SFRD_TRY(dense_weights<T>(p, dLduT, p.ws + p.off_D, true, s));
+    SFRD_TRY(run_x<T>(p, MODE_PLAIN, D, W2, p.pitch, 0.0, s));
+    if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
+    SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, W2, UB, 1.0 / C, s));
+
+    const size_t per_step = 9 * L.fld;   // u^, F1..F4, u, a, b, c
+    for (int64_t seg = L.nseg - 1; seg >= 0; --seg) {
+        const int64_t k0 = seg * K;
+        const int64_t ns = k0 + K <= nsteps ? K : nsteps - k0;
+        // recompute the segment from its checkpoint, saving every step's intermediates
+        SFRD_TRY(cudaMemcpyAsync(p.ws + p.off_U, aws + L.off_ckpt + seg * L.fld, L.fld, cudaMemcpyDeviceToDevice, s));
+        SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, internal_arr<T>(p, p.off_U), W, 1.0 / C, s));
+        SFRD_TRY(launch_set_clock(p, t0, s, k0));
+        for (int64_t j = 0; j < ns; ++j) {
+            char* st = aws + L.off_seg + j * per_step;
+            SFRD_TRY(cudaMemcpyAsync(st, p.ws + p.off_U, L.fld, cudaMemcpyDeviceToDevice, s));
+            StepSave sv;
+            for (int q = 0; q < 4; ++q) {
+                sv.F[q] = st + (1 + q) * L.fld;
+                sv.stage[q] = st + (5 + q) * L.fld;
+            }
+            SFRD_TRY(step_impl<T>(p, s, nullptr, nullptr, 0, &sv));
+        }
+        // reverse sweep over the segment
+        for (int64_t j = ns - 1; j >= 0; --j) {
+            char* st = aws + L.off_seg + j * per_step;
+            auto patch = [&](ColArgs<T>& a) {
+                a.U = reinterpret_cast<T*>(st);
+                a.F1 = reinterpret_cast<T*>(st + 1 * L.fld);
+                a.F2 = reinterpret_cast<T*>(st + 2 * L.fld);
+                a.F3 = reinterpret_cast<T*>(st + 3 * L.fld);
+                a.F4 = reinterpret_cast<T*>(st + 4 * L.fld);
+                a.Ub = ub;
+                a.Cb = cb;
+                a.Bb = bb;
+                a.Ab = ab;
+                a.grad = grad;
+            };
+            auto slow_pass = [&](int mode, const Arr<T>& in) -> cudaError_t {
+                dim3 grid;
+                ColArgs<T> a = col_args<T>(p, slow, in, W, 1.0, grid);
+                patch(a);
+                return launch_col<T>(p, slow, mode, a, grid, s);
+            };
+            auto x_pass = [&](int stage) -> cudaError_t {
+                dim3 grid;
+                XArgs<T> a = x_args<T>(p, W, W, p.pitch, 0.0, grid);
+                a.state = reinterpret_cast<const T*>(st + (5 + stage) * L.fld);
+                a.grad = grad;
+                return launch_x<T>(p, MODE_XADJ, a, grid, s);
+            };
+            auto chain = [&](int stage) -> cudaError_t {
+                if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W, W, 1.0, s));
+                SFRD_TRY(x_pass(stage));
+                if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W, W, 1.0, s));
+                return cudaSuccess;
+            };
+            SFRD_TRY(slow_pass(MODE_ADJ_ENTRY, UB));
+            SFRD_TRY(chain(3));
+            SFRD_TRY(slow_pass(MODE_ADJ_CB, W));
+            SFRD_TRY(chain(2));
+            SFRD_TRY(slow_pass(MODE_ADJ_BA, W));
+            SFRD_TRY(chain(1));
+            SFRD_TRY(slow_pass(MODE_ADJ_AU, W));
+            SFRD_TRY(chain(0));
+            SFRD_TRY(slow_pass(MODE_ADJ_EXIT, W));
+        }
+    }
+    // exit: dL/du0 = w .* T(Ub~)
+    SFRD_TRY(run_x<T>(p, MODE_PLAIN, UB, W2, p.pitch, 0.0, s));
+    if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
+    SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, W2, D, 1.0, s));
+    return dense_weights<T>(p, p.ws + p.off_D, dLdu0, false, s);
+}
+
 #define SFRD_INSTANTIATE(T)                                                                  \
     template cudaError_t launch_step<T>(Plan&, cudaStream_t);                                \
     template cudaError_t launch_step_profiled<T>(Plan&, cudaStream_t, cudaEvent_t*, int*, int); \
@@ -652,6 +852,10 @@ cudaError_t launch_coef_copy(Plan& p, int which, void* out, cudaStream_t s) {
     template cudaError_t launch_inverse<T>(Plan&, const void*, void*, cudaStream_t);         \
     template cudaError_t launch_coef_init<T>(Plan&, cudaStream_t);                           \
     template cudaError_t launch_coef_copy<T>(Plan&, int, void*, cudaStream_t);          \
-    template cudaError_t prepare_kernels<T>(const Plan&);
+    template cudaError_t prepare_kernels<T>(const Plan&);                                  \
+    template cudaError_t launch_run_checkpointed<T>(Plan&, void*, double, int64_t, int64_t, char*,       \
+                                                    const AdjLayout&, cudaStream_t);                      \
+    template cudaError_t launch_adjoint<T>(Plan&, double, int64_t, int64_t, char*, const AdjLayout&,     \
+                                           const void*, void*, cudaStream_t);
 
 }  // namespace sfrd

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kThreads, 3) col2_kernel(const ColArgs<T> a) {
                 } else {  // MODE_TD
                     const T R = a.CR[4 * i], p1 = a.CR[4 * i + 1], p2 = a.CR[4 * i + 2], p3 = a.CR[4 * i + 3];
                     const T un = R * a.U[i] + p1 * a.F1[i] + p2 * (a.F2[i] + a.F3[i]) + p3 * F[h];
+                    if (a.F4) a.F4[i] = F[h];
                     a.U[i] = un;
                     s[h] = un;
                 }
@@ -175,24 +176,36 @@ __global__ void __launch_bounds__(kThreads, 3) x2_kernel(const XArgs<T> a) {
     if (MODE == MODE_REACT) {
         E::post(buf, red, red2, bc, c, g, [&](int i, C v) { buf[i * LD + c] = v; });
         __syncthreads();
-        // pointwise reaction on the physical values (kept out of the unrolled code)
+        // pointwise reaction on the physical values (kept out of the unrolled code);
+        // a warp walks 32 consecutive x of one row, so the optional stage save is coalesced
         const double t = a.clock->t0 + ((double)a.clock->k + a.stage_frac) * a.tau;
-        const int rA = r0 + c, rB = rA + shiftB;
+        constexpr int NW = kThreads / 32, RW = (CC + NW - 1) / NW;
+        const int w = tid >> 5, l = tid & 31;
 #pragma unroll 1
-        for (int i = g; i < n; i += G) {
-            const C v = buf[i * LD + c];
-            C f;
-            if (a.S == 2) {
-                react2<T>(a.re, v.x, v.y, f.x, f.y);
-            } else {
-                const double x = ax.lo + (ax.node0 + i) * ax.h;
-                const int yA = rA % a.ny, yB = rB % a.ny;
-                const double ya = a.ay.lo + (a.ay.node0 + yA) * a.ay.h;
-                const double yb = a.ay.lo + (a.ay.node0 + yB) * a.ay.h;
-                f.x = react1<T>(a.re, v.x, x, ya, t);
-                f.y = react1<T>(a.re, v.y, x, yb, t);
+        for (int rr = 0; rr < RW; ++rr) {
+            const int cc = w + rr * NW;
+            if (cc >= CC) continue;
+            const int rA = r0 + cc, rB = rA + shiftB;
+            T* sv = a.save ? a.save + (long long)rA * a.out_pitch : nullptr;
+            const double ya = a.ay.lo + (a.ay.node0 + rA % a.ny) * a.ay.h;
+            const double yb = a.ay.lo + (a.ay.node0 + rB % a.ny) * a.ay.h;
+#pragma unroll 1
+            for (int x = l; x < n; x += 32) {
+                const C v = buf[x * LD + cc];
+                if (sv) {
+                    if (rA < a.rows) sv[x] = v.x;
+                    if (rB < a.rows) sv[a.out_offB + x] = v.y;
+                }
+                C f;
+                if (a.S == 2) {
+                    react2<T>(a.re, v.x, v.y, f.x, f.y);
+                } else {
+                    const double xc = ax.lo + (ax.node0 + x) * ax.h;
+                    f.x = react1<T>(a.re, v.x, xc, ya, t);
+                    f.y = react1<T>(a.re, v.y, xc, yb, t);
+                }
+                buf[x * LD + cc] = f;
             }
-            buf[i * LD + c] = f;
         }
         __syncthreads();
         E::forward(buf, red2, bc, tws, twstride, c, g);

@@ -68,4 +68,73 @@ __device__ __forceinline__ T react1(const ReactDev& re, T u, double x, double y,
     }
 }
 
+// ---- transposed Jacobians and parameter derivatives (for the discrete adjoint) -------
+//
+// (gu, gv) = J_f(u, v)^T (yu, yv), and dp[q] += w * sum_s (d f_s / d p_q) y_s for the
+// parameter vector p of the reaction kind (order as in sfrd.h).
+template <typename T>
+__device__ __forceinline__ void react2_vjp(const ReactDev& re, T u, T v, T yu, T yv, T& gu, T& gv, double w,
+                                           double* dp) {
+    switch (re.kind) {
+        case SFRD_REACT_FHN: {
+            const T mu = (T)re.p[0], eps = (T)re.p[1], beta = (T)re.p[2], gam = (T)re.p[3], del = (T)re.p[4];
+            const T fuu = -(T)3 * u * u + (T)2 * ((T)1 + mu) * u - mu;
+            gu = fuu * yu + eps * beta * yv;
+            gv = -yu - eps * gam * yv;
+            dp[0] += w * (double)(-u * ((T)1 - u) * yu);                   // d f_u / d mu
+            dp[1] += w * (double)((beta * u - gam * v - del) * yv);        // d f_v / d eps
+            dp[2] += w * (double)(eps * u * yv);                            // d f_v / d beta
+            dp[3] += w * (double)(-eps * v * yv);                           // d f_v / d gamma
+            dp[4] += w * (double)(-eps * yv);                               // d f_v / d delta
+        } break;
+        case SFRD_REACT_GRAY_SCOTT: {
+            const T F = (T)re.p[0], K = (T)re.p[1];
+            gu = (-v * v - F) * yu + v * v * yv;
+            gv = (-(T)2 * u * v) * yu + ((T)2 * u * v - (F + K)) * yv;
+            dp[0] += w * (double)(((T)1 - u) * yu - v * yv);
+            dp[1] += w * (double)(-v * yv);
+        } break;
+        case SFRD_REACT_SCHNAKENBERG: {
+            const T g = (T)re.p[0], a = (T)re.p[1], b = (T)re.p[2];
+            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
+            gu = g * (-(T)1 + (T)2 * U * V) * yu - g * (T)2 * U * V * yv;
+            gv = g * U * U * yu - g * U * U * yv;
+            dp[0] += w * (double)((a - U + U * U * V) * yu + (b - U * U * V) * yv);
+            dp[1] += w * (double)(g * yu);
+            dp[2] += w * (double)(g * yv);
+        } break;
+        case SFRD_REACT_GIERER_MEINHARDT: {
+            const T c1 = (T)re.p[0], c2 = (T)re.p[1], c3 = (T)re.p[2], c4 = (T)re.p[3];
+            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
+            gu = ((T)2 * c1 * U / V - c2) * yu + (T)2 * c3 * U * yv;
+            gv = (-c1 * U * U / (V * V)) * yu - c4 * yv;
+            dp[0] += w * (double)(U * U / V * yu);
+            dp[1] += w * (double)(-U * yu);
+            dp[2] += w * (double)(U * U * yv);
+            dp[3] += w * (double)(-V * yv);
+        } break;
+        case SFRD_REACT_LINEAR:
+            gu = (T)re.p[0] * yu;
+            gv = (T)re.p[0] * yv;
+            dp[0] += w * (double)(u * yu + v * yv);
+            break;
+        default:
+            gu = 0;
+            gv = 0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T react1_vjp(const ReactDev& re, T u, T y, double w, double* dp) {
+    switch (re.kind) {
+        case SFRD_REACT_LINEAR:
+            dp[0] += w * (double)(u * y);
+            return (T)re.p[0] * y;
+        case SFRD_REACT_HUXLEY_MMS:
+            return ((T)1 - u) * ((T)3 * u - (T)1) * y;   // d/du [u (1-u)(u-1)]; the source has no u
+        default:
+            return 0;
+    }
+}
+
 }  // namespace sfrd

@@ -24,13 +24,13 @@ static int cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
     } while (0)
 
-__global__ void set_clock_kernel(Clock* c, double t0) {
+__global__ void set_clock_kernel(Clock* c, double t0, long long k0) {
     c->t0 = t0;
-    c->k = 0;
+    c->k = k0;
 }
 
-cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s) {
-    set_clock_kernel<<<1, 1, 0, s>>>(reinterpret_cast<Clock*>(p.ws + p.off_clock), t0);
+cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s, long long k0) {
+    set_clock_kernel<<<1, 1, 0, s>>>(reinterpret_cast<Clock*>(p.ws + p.off_clock), t0, k0);
     return cudaGetLastError();
 }
 
@@ -270,6 +270,30 @@ static int create(Plan** out, const sfrd_grid* g, int bc, const double* alpha, c
     p->ws_bytes = o;
     *out = p;
     return SFRD_OK;
+}
+
+AdjLayout adj_layout(const Plan& p, int64_t nsteps, int64_t K) {
+    AdjLayout L;
+    L.nsteps = nsteps;
+    L.K = K;
+    L.nseg = (nsteps + K - 1) / K;
+    L.fld = align_up((size_t)p.S * p.plane * p.esize, 256);
+    size_t o = 0;
+    L.off_Ub = o; o += L.fld;
+    L.off_Cb = o; o += L.fld;
+    L.off_Bb = o; o += L.fld;
+    L.off_Ab = o; o += L.fld;
+    L.off_ckpt = o; o += (size_t)L.nseg * L.fld;
+    L.off_seg = o; o += (size_t)K * 9 * L.fld;
+    L.off_grad = o; o += 256;
+    L.bytes = o;
+    return L;
+}
+
+static bool adjoint_capable(const Plan& p) {
+    for (int d = 0; d < p.dim; ++d)
+        if (!p.v2[d]) return false;
+    return true;
 }
 
 static void drop_graph(Plan* p) {
@@ -522,6 +546,56 @@ int sfrd_profile_step(sfrd_plan_t plan, int32_t cap, float* ms, int32_t* kind) {
     }
     for (auto& x : ev) cudaEventDestroy(x);
     return e == cudaSuccess ? SFRD_OK : sfrd::cuda_fail(e, "sfrd_profile_step");
+}
+
+int sfrd_adjoint_workspace_bytes(sfrd_plan_t plan, int64_t nsteps, int64_t ckpt_every, size_t* bytes) {
+    if (!plan || !bytes || nsteps < 1 || ckpt_every < 1) return SFRD_EINVAL;
+    if (!sfrd::adjoint_capable(plan->p)) return SFRD_EUNSUPPORTED;
+    *bytes = sfrd::adj_layout(plan->p, nsteps, ckpt_every).bytes;
+    return SFRD_OK;
+}
+
+int sfrd_run_checkpointed(sfrd_plan_t plan, void* u, double t0, int64_t nsteps, int64_t ckpt_every, void* adj_ws,
+                          size_t adj_bytes) {
+    if (!plan || !u || nsteps < 1 || ckpt_every < 1) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (!sfrd::adjoint_capable(p)) return SFRD_EUNSUPPORTED;
+    if (!p.ws) return SFRD_ENOWS;
+    const sfrd::AdjLayout L = sfrd::adj_layout(p, nsteps, ckpt_every);
+    if (!adj_ws || adj_bytes < L.bytes || (reinterpret_cast<uintptr_t>(adj_ws) & 255u)) return SFRD_ENOWS;
+    cudaError_t e = p.dtype == SFRD_F32
+        ? sfrd::launch_run_checkpointed<float>(p, u, t0, nsteps, ckpt_every, static_cast<char*>(adj_ws), L, p.stream)
+        : sfrd::launch_run_checkpointed<double>(p, u, t0, nsteps, ckpt_every, static_cast<char*>(adj_ws), L, p.stream);
+    if (e != cudaSuccess) return sfrd::cuda_fail(e, "sfrd_run_checkpointed");
+    p.loaded = true;
+    return SFRD_OK;
+}
+
+int sfrd_adjoint(sfrd_plan_t plan, double t0, int64_t nsteps, int64_t ckpt_every, void* adj_ws, size_t adj_bytes,
+                 const void* dLduT, void* dLdu0, double* dLdalpha, double* dLdkappa, double* dLdparams) {
+    if (!plan || !dLduT || !dLdu0 || nsteps < 1 || ckpt_every < 1) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (!sfrd::adjoint_capable(p)) return SFRD_EUNSUPPORTED;
+    if (!p.ws) return SFRD_ENOWS;
+    const sfrd::AdjLayout L = sfrd::adj_layout(p, nsteps, ckpt_every);
+    if (!adj_ws || adj_bytes < L.bytes || (reinterpret_cast<uintptr_t>(adj_ws) & 255u)) return SFRD_ENOWS;
+    char* aws = static_cast<char*>(adj_ws);
+    cudaError_t e = p.dtype == SFRD_F32
+        ? sfrd::launch_adjoint<float>(p, t0, nsteps, ckpt_every, aws, L, dLduT, dLdu0, p.stream)
+        : sfrd::launch_adjoint<double>(p, t0, nsteps, ckpt_every, aws, L, dLduT, dLdu0, p.stream);
+    if (e != cudaSuccess) return sfrd::cuda_fail(e, "sfrd_adjoint");
+    double g[16];
+    e = cudaMemcpyAsync(g, aws + L.off_grad, sizeof(g), cudaMemcpyDeviceToHost, p.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+    if (e != cudaSuccess) return sfrd::cuda_fail(e, "sfrd_adjoint (gradients)");
+    for (int s = 0; s < p.S; ++s) {
+        if (dLdkappa) dLdkappa[s] = g[s];
+        if (dLdalpha) dLdalpha[s] = g[2 + s];
+    }
+    if (dLdparams)
+        for (int q = 0; q < 8; ++q) dLdparams[q] = q < 5 ? g[4 + q] : 0.0;
+    p.loaded = false;   // the work arrays were reused
+    return SFRD_OK;
 }
 
 void sfrd_destroy(sfrd_plan_t plan) {

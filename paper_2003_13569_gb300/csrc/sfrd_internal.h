@@ -50,6 +50,13 @@ enum PassMode {
     MODE_TC = 4,     // slow axis: F3 <- T(in); out = T(Q(Q U + phi F1) + phi(2F3 - F1))/C
     MODE_TD = 5,     // slow axis: U <- R U + phi1 F1 + phi2 (F2+F3) + phi3 T(in); out = T(U)/C
     MODE_REACT = 6,  // contiguous axis: out = T(f(T(in)))
+    // discrete adjoint (register engine only; tilde-frame cotangents, see adjoint.cuh)
+    MODE_XADJ = 7,       // contiguous axis: out = T(J_f(state)^T T(in)); accumulates dL/dparams
+    MODE_ADJ_ENTRY = 8,  // slow axis: out = T(phi3 Ub)
+    MODE_ADJ_CB = 9,     // slow axis: Cb = T(in)/C; out = T(phi2 Ub + 2 phi Cb)
+    MODE_ADJ_BA = 10,    // slow axis: Bb = T(in)/C; out = T(phi2 Ub + phi Bb)
+    MODE_ADJ_AU = 11,    // slow axis: Ab = Q Cb + T(in)/C; out = T(phi1 Ub - phi Cb + phi Ab)
+    MODE_ADJ_EXIT = 12,  // slow axis: Ub <- R Ub + Q Bb + Q Ab + T(in)/C
 };
 
 // Pass kinds reported by the per-launch profile of one step.
@@ -77,6 +84,18 @@ struct ColArgs {
     const T* CR;          // interleaved (R13, phi1, phi2, phi3) quads
     Clock* clock;         // TD advances k
     AxisDev ax;
+    T* F4;                // MODE_TD: F(f_c) of the step is also stored here when non-null
+    // adjoint
+    T* Ub;                // spectral cotangent of the state (tilde frame), read; updated by ADJ_EXIT
+    T* Cb;
+    T* Bb;
+    T* Ab;
+    double* grad;         // [0,1] dL/dkappa_s, [2,3] dL/dalpha_s (atomic accumulation)
+    const double* lam[3]; // eigenvalue tables (x, y, z)
+    int nk[3];            // unknowns per axis (x, y, z)
+    int dim;
+    int S;
+    double alpha[2], kappa[2], tau;
 };
 
 template <typename T>
@@ -93,6 +112,10 @@ struct XArgs {
     const Clock* clock;
     AxisDev ax, ay, az;
     ReactDev re;
+    T* save;              // MODE_REACT: physical stage values also stored here when non-null
+    const T* state;       // MODE_XADJ: stored physical stage values (same layout as in/out)
+    double* grad;         // MODE_XADJ: dL/dparams accumulators [8]
+    int nz;
 };
 
 // Host-side plan.
@@ -153,8 +176,29 @@ constexpr int cc_for(bool f64, int N) { return f64 ? (N >= 1024 ? 4 : 8) : (N >=
 template <typename T, int N> cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s);
 template <typename T, int N> cudaError_t x2_launch(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s);
 template <typename T, int N> cudaError_t prepare2();
+template <typename T, int N> cudaError_t adj_col_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s);
+template <typename T, int N> cudaError_t adj_x_launch(const XArgs<T>& a, dim3 grid, cudaStream_t s);
+template <typename T, int N> cudaError_t prepare_adj();
 }  // namespace v2
-cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s);
+
+// Per-launch array overrides used by the checkpointed forward recomputation.
+struct StepSave {
+    void* F[4];       // F(f_u), F(f_a), F(f_b), F(f_c) of the step
+    void* stage[4];   // physical u, a, b, c of the step (internal layout)
+};
+
+// Adjoint workspace layout (caller-provided buffer).
+struct AdjLayout {
+    int64_t nsteps = 0, K = 0, nseg = 0;
+    size_t off_Ub = 0, off_Cb = 0, off_Bb = 0, off_Ab = 0, off_ckpt = 0, off_seg = 0, off_grad = 0, bytes = 0;
+    size_t fld = 0;   // bytes of one S-species internal array
+};
+AdjLayout adj_layout(const Plan& p, int64_t nsteps, int64_t K);
+template <typename T> cudaError_t launch_run_checkpointed(Plan& p, void* u, double t0, int64_t nsteps, int64_t K,
+                                                          char* aws, const AdjLayout& L, cudaStream_t s);
+template <typename T> cudaError_t launch_adjoint(Plan& p, double t0, int64_t nsteps, int64_t K, char* aws,
+                                                 const AdjLayout& L, const void* dLduT, void* dLdu0, cudaStream_t s);
+cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s, long long k0 = 0);
 
 int kernels_per_step(const Plan& p);
 

@@ -1,8 +1,9 @@
 // Register-FFT passes, F64, axis length 1024.
-#include "passes2.cuh"
+#include "adjoint.cuh"
 
 namespace sfrd {
 namespace v2 {
 SFRD_V2_INSTANTIATE(double, 1024)
+SFRD_ADJ_INSTANTIATE(double, 1024)
 }  // namespace v2
 }  // namespace sfrd
