@@ -176,36 +176,29 @@ __global__ void __launch_bounds__(kThreads, 3) x2_kernel(const XArgs<T> a) {
     if (MODE == MODE_REACT) {
         E::post(buf, red, red2, bc, c, g, [&](int i, C v) { buf[i * LD + c] = v; });
         __syncthreads();
-        // pointwise reaction on the physical values (kept out of the unrolled code);
-        // a warp walks 32 consecutive x of one row, so the optional stage save is coalesced
+        // pointwise reaction on the physical values (kept out of the unrolled code)
         const double t = a.clock->t0 + ((double)a.clock->k + a.stage_frac) * a.tau;
-        constexpr int NW = kThreads / 32, RW = (CC + NW - 1) / NW;
-        const int w = tid >> 5, l = tid & 31;
+        const int rA = r0 + c, rB = rA + shiftB;
+        T* sv = a.save ? a.save + (long long)rA * a.out_pitch : nullptr;   // stage save (adjoint recomputation)
 #pragma unroll 1
-        for (int rr = 0; rr < RW; ++rr) {
-            const int cc = w + rr * NW;
-            if (cc >= CC) continue;
-            const int rA = r0 + cc, rB = rA + shiftB;
-            T* sv = a.save ? a.save + (long long)rA * a.out_pitch : nullptr;
-            const double ya = a.ay.lo + (a.ay.node0 + rA % a.ny) * a.ay.h;
-            const double yb = a.ay.lo + (a.ay.node0 + rB % a.ny) * a.ay.h;
-#pragma unroll 1
-            for (int x = l; x < n; x += 32) {
-                const C v = buf[x * LD + cc];
-                if (sv) {
-                    if (rA < a.rows) sv[x] = v.x;
-                    if (rB < a.rows) sv[a.out_offB + x] = v.y;
-                }
-                C f;
-                if (a.S == 2) {
-                    react2<T>(a.re, v.x, v.y, f.x, f.y);
-                } else {
-                    const double xc = ax.lo + (ax.node0 + x) * ax.h;
-                    f.x = react1<T>(a.re, v.x, xc, ya, t);
-                    f.y = react1<T>(a.re, v.y, xc, yb, t);
-                }
-                buf[x * LD + cc] = f;
+        for (int i = g; i < n; i += G) {
+            const C v = buf[i * LD + c];
+            if (sv) {
+                if (rA < a.rows) sv[i] = v.x;
+                if (rB < a.rows) sv[a.out_offB + i] = v.y;
             }
+            C f;
+            if (a.S == 2) {
+                react2<T>(a.re, v.x, v.y, f.x, f.y);
+            } else {
+                const double x = ax.lo + (ax.node0 + i) * ax.h;
+                const int yA = rA % a.ny, yB = rB % a.ny;
+                const double ya = a.ay.lo + (a.ay.node0 + yA) * a.ay.h;
+                const double yb = a.ay.lo + (a.ay.node0 + yB) * a.ay.h;
+                f.x = react1<T>(a.re, v.x, x, ya, t);
+                f.y = react1<T>(a.re, v.y, x, yb, t);
+            }
+            buf[i * LD + c] = f;
         }
         __syncthreads();
         E::forward(buf, red2, bc, tws, twstride, c, g);
