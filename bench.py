@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batched-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -277,6 +278,29 @@ def main():
                          "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
         extra["fp32_vs_fp64_rel_l2"] = {"value": err, "steps": args.fp64_steps}
         del s64
+        torch.cuda.empty_cache()
+
+    # the batched workload: 256 Gierer-Meinhardt instances, one persistent launch per pass
+    if rank == 0 and args.batched_steps > 0:
+        cfgs = W.gm_instances(256, seed=3)
+        bt = sf.Batch(cfgs, dtype="f32")
+        bt.load([np.stack(W.initial_fields(c)) for c in cfgs])
+        bt.advance(3)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(bt.stream)
+        bt.advance(args.batched_steps)
+        b1.record(bt.stream)
+        torch.cuda.synchronize()
+        msb = b0.elapsed_time(b1)
+        sides = sorted(set(int(c["N"][0]) for c in cfgs))
+        extra["batched"] = {"value": bt.dof * args.batched_steps / (msb * 1e-3), "unit": "DOF-steps/s",
+                            "ms_per_step": msb / args.batched_steps, "steps": args.batched_steps,
+                            "instances": bt.count, "dof": bt.dof, "launches_per_step": bt.launches_per_step,
+                            "workload": "2D fractional Gierer-Meinhardt, 256 instances, sides %s, BC P/D/N and "
+                                        "alpha U(1.2,2] per instance, dt=0.05, FP32" % sides}
+        del bt
         torch.cuda.empty_cache()
 
     # end to end through host memory: pinned input -> device -> K steps -> pinned output

@@ -220,6 +220,27 @@ int sfrd_run_checkpointed(sfrd_plan_t plan, void* u, double t0, int64_t nsteps, 
 int sfrd_adjoint(sfrd_plan_t plan, double t0, int64_t nsteps, int64_t ckpt_every, void* adj_ws, size_t adj_bytes,
                  const void* dLduT, void* dLdu0, double* dLdalpha, double* dLdkappa, double* dLdparams);
 
+/* ---- batched instances ---------------------------------------------------
+ * count independent problems of the same dimension, species count, reaction
+ * kind/parameters, dtype and time step, each with its own grid (intervals per
+ * axis <= 512), boundary condition bcs[i] and coefficients alpha[i*S+s],
+ * kappa[i*S+s].  One ETDRK4-P13 step of all instances is one persistent launch
+ * per pass (8 in 2D, 16 in 3D) replayed from a captured CUDA graph; each
+ * launch's blocks draw (instance, tile) work items, longest lines first.
+ * Fields are passed as host arrays of count device pointers, field i laid out
+ * [S][...] for instance i's grid.  Errors as for single plans. */
+typedef struct sfrd_batch_s* sfrd_batch_t;
+int sfrd_batch_plan(sfrd_batch_t* out, int64_t count, const sfrd_grid* grids, const int32_t* bcs,
+                    const double* alpha, const double* kappa, double dt, int32_t dtype,
+                    const sfrd_reaction* reaction);
+int sfrd_batch_workspace_bytes(sfrd_batch_t batch, size_t* bytes);
+int sfrd_batch_bind(sfrd_batch_t batch, void* workspace, size_t bytes, void* stream);
+int sfrd_batch_load(sfrd_batch_t batch, const void* const* u0, double t0);
+int sfrd_batch_advance(sfrd_batch_t batch, int64_t nsteps);
+int sfrd_batch_store(sfrd_batch_t batch, void* const* u);
+int sfrd_batch_info(sfrd_batch_t batch, int64_t* count, int64_t* dof, int64_t* launches_per_step);
+void sfrd_batch_destroy(sfrd_batch_t batch);
+
 /* Release the plan and its CUDA graph (not the workspace). */
 void sfrd_destroy(sfrd_plan_t plan);
 

@@ -32,7 +32,9 @@ COEFFICIENTS = ("R13", "Q13", "phi", "phi1", "phi2", "phi3")
 EXPORTS = ("sfrd_plan", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
            "sfrd_store", "sfrd_run", "sfrd_step", "sfrd_run_host", "sfrd_forward", "sfrd_inverse",
            "sfrd_coefficients", "sfrd_profile_step", "sfrd_adjoint_workspace_bytes", "sfrd_run_checkpointed",
-           "sfrd_adjoint", "sfrd_destroy", "sfrd_strerror", "sfrd_last_error")
+           "sfrd_adjoint", "sfrd_batch_plan", "sfrd_batch_workspace_bytes", "sfrd_batch_bind", "sfrd_batch_load",
+           "sfrd_batch_advance", "sfrd_batch_store", "sfrd_batch_info", "sfrd_batch_destroy", "sfrd_destroy",
+           "sfrd_strerror", "sfrd_last_error")
 
 
 class Grid(ctypes.Structure):
@@ -80,8 +82,19 @@ _lib.sfrd_strerror.argtypes = [ctypes.c_int]
 _lib.sfrd_strerror.restype = ctypes.c_char_p
 _lib.sfrd_last_error.argtypes = []
 _lib.sfrd_last_error.restype = ctypes.c_char_p
+_lib.sfrd_batch_plan.argtypes = [ctypes.POINTER(_P), ctypes.c_int64, ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(_D), ctypes.POINTER(_D), _D, ctypes.c_int32, ctypes.POINTER(Reaction)]
+_lib.sfrd_batch_workspace_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+_lib.sfrd_batch_bind.argtypes = [_P, _P, ctypes.c_size_t, _P]
+_lib.sfrd_batch_load.argtypes = [_P, ctypes.POINTER(_P), _D]
+_lib.sfrd_batch_advance.argtypes = [_P, ctypes.c_int64]
+_lib.sfrd_batch_store.argtypes = [_P, ctypes.POINTER(_P)]
+_lib.sfrd_batch_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64)]
+_lib.sfrd_batch_destroy.argtypes = [_P]
+_lib.sfrd_batch_destroy.restype = None
 for _name in EXPORTS:
-    if _name not in ("sfrd_destroy", "sfrd_strerror", "sfrd_last_error"):
+    if _name not in ("sfrd_destroy", "sfrd_batch_destroy", "sfrd_strerror", "sfrd_last_error"):
         getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -281,6 +294,98 @@ class Solver:
     def close(self):
         if getattr(self, "handle", None):
             _lib.sfrd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched instances -----------------------------------------------------------
+
+class Batch:
+    """Many independent instances (same dim, species, reaction, dt, dtype; own grid, BC, alpha,
+    kappa) stepped together, one persistent launch per pass."""
+
+    def __init__(self, cfgs: list, dtype: str | None = None, device=None):
+        import torch
+        self.torch = torch
+        self.cfgs = cfgs
+        self.dtype = dtype or cfgs[0]["dtype"]
+        self.tdtype = torch.float32 if self.dtype == "f32" else torch.float64
+        n = len(cfgs)
+        S = len(cfgs[0]["alpha"])
+        self.S = S
+        grids = (Grid * n)()
+        bcs = (ctypes.c_int32 * n)()
+        al = (ctypes.c_double * (n * S))()
+        ka = (ctypes.c_double * (n * S))()
+        self.shapes = []
+        for i, c in enumerate(cfgs):
+            g = grids[i]
+            g.dim = c["dim"]
+            for d in range(3):
+                g.N[d] = int(c["N"][d]) if d < c["dim"] else 1
+                g.lo[d] = float(c["lo"][d]) if d < c["dim"] else 0.0
+                g.hi[d] = float(c["hi"][d]) if d < c["dim"] else 1.0
+            bcs[i] = BC[c["bc"]]
+            for s in range(S):
+                al[i * S + s] = float(c["alpha"][s])
+                ka[i * S + s] = float(c["kappa"][s])
+            unk = {"periodic": 0, "dirichlet": -1, "neumann": 1}[c["bc"]]
+            self.shapes.append(tuple([S] + [int(c["N"][d]) + unk for d in reversed(range(c["dim"]))]))
+        r0 = cfgs[0]["reaction"]
+        r = Reaction()
+        r.kind = REACTION[r0["kind"]]
+        r.nspecies = S
+        for i, v in enumerate(r0.get("p", [])):
+            r.p[i] = float(v)
+        off = r0.get("offset", (0.0, 0.0))
+        r.offset[0], r.offset[1] = float(off[0]), float(off[1])
+        h = ctypes.c_void_p()
+        _check(_lib.sfrd_batch_plan(ctypes.byref(h), n, grids, bcs, al, ka, float(cfgs[0]["dt"]),
+                                    DTYPE[self.dtype], ctypes.byref(r)), "sfrd_batch_plan")
+        self.handle = h
+        nb = ctypes.c_size_t()
+        _check(_lib.sfrd_batch_workspace_bytes(h, ctypes.byref(nb)), "sfrd_batch_workspace_bytes")
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.ws = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device=self.device)
+        ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.stream = torch.cuda.current_stream(self.device)
+        _check(_lib.sfrd_batch_bind(h, ctypes.c_void_p(ptr), int(nb.value), ctypes.c_void_p(self.stream.cuda_stream)),
+               "sfrd_batch_bind")
+        cnt, dof, lps = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.sfrd_batch_info(h, ctypes.byref(cnt), ctypes.byref(dof), ctypes.byref(lps)), "sfrd_batch_info")
+        self.count, self.dof, self.launches_per_step = cnt.value, dof.value, lps.value
+
+    def _ptrs(self, fields):
+        arr = (_P * self.count)()
+        for i, f in enumerate(fields):
+            arr[i] = f.data_ptr()
+        return arr
+
+    def load(self, fields, t0=0.0):
+        t = self.torch
+        self._keep = [t.as_tensor(np.asarray(f) if not isinstance(f, t.Tensor) else f).to(
+            device=self.device, dtype=self.tdtype).contiguous() for f in fields]
+        for f, shp in zip(self._keep, self.shapes):
+            if tuple(f.shape) != shp:
+                raise ValueError("field shape %s, expected %s" % (tuple(f.shape), shp))
+        _check(_lib.sfrd_batch_load(self.handle, self._ptrs(self._keep), float(t0)), "sfrd_batch_load")
+
+    def advance(self, nsteps):
+        _check(_lib.sfrd_batch_advance(self.handle, int(nsteps)), "sfrd_batch_advance")
+
+    def store(self):
+        outs = [self.torch.empty(shp, dtype=self.tdtype, device=self.device) for shp in self.shapes]
+        _check(_lib.sfrd_batch_store(self.handle, self._ptrs(outs)), "sfrd_batch_store")
+        return outs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.sfrd_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

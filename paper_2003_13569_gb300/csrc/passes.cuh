@@ -53,18 +53,18 @@ __device__ __forceinline__ C get_one(const C* buf, int ldb, const AxisDev& ax, i
 
 // ---- strided-axis pass (y or z): tile = all unknowns along the axis x CC columns ----
 
+// Body of the strided pass for tile (bx, by); smem = dynamic shared memory of the block.
 template <typename T, int CC, int MODE>
-__global__ void __launch_bounds__(kThreads) col_kernel(const ColArgs<T> a) {
+__device__ __forceinline__ void col_body(const ColArgs<T>& a, int bx, int by, unsigned char* smem_raw) {
     using C = typename Cx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     constexpr int ldb = CC + 1;
     constexpr int G = kThreads / CC;
     const int tid = threadIdx.x, c = tid % CC, grp = tid / CC;
     const AxisDev& ax = a.ax;
-    const int xA = blockIdx.x * a.xw + c;
+    const int xA = bx * a.xw + c;
     const int xB = xA + a.bshift;
-    const long long other = blockIdx.y;
+    const long long other = by;
 
     // load along the axis, natural order, with the odd/even extension
     {
@@ -160,15 +160,20 @@ __global__ void __launch_bounds__(kThreads) col_kernel(const ColArgs<T> a) {
             if (okB) qA[i * a.out_sAxis + a.out_offB] = v.y;
         }
     }
-    if (MODE == MODE_TD && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) a.clock->k += 1;
+    if (MODE == MODE_TD && bx == 0 && by == 0 && threadIdx.x == 0) a.clock->k += 1;
+}
+
+template <typename T, int CC, int MODE>
+__global__ void __launch_bounds__(kThreads) col_kernel(const ColArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    col_body<T, CC, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ---- contiguous-axis pass: tile = CC row pairs (species 0 / species 1, or two rows) ----
 
 template <typename T, int CC, int MODE>
-__global__ void __launch_bounds__(kThreads) x_kernel(const XArgs<T> a) {
+__device__ __forceinline__ void x_body(const XArgs<T>& a, int bx, unsigned char* smem_raw) {
     using C = typename Cx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     constexpr int ldb = CC + 1;
     constexpr int G = kThreads / CC;
@@ -176,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) x_kernel(const XArgs<T> a) {
     const AxisDev& ax = a.ax;
     const int n = ax.n;
     const int shiftB = (a.S == 2) ? 0 : CC;
-    const int r0 = blockIdx.x * (a.S == 2 ? CC : 2 * CC);
+    const int r0 = bx * (a.S == 2 ? CC : 2 * CC);
 
     // transposed load: consecutive threads read consecutive x of one row
     for (int q = tid; q < CC * n; q += kThreads) {
@@ -244,6 +249,12 @@ __global__ void __launch_bounds__(kThreads) x_kernel(const XArgs<T> a) {
             if (rB2 < a.rows) a.out[(long long)rA2 * a.out_pitch + a.out_offB + i] = (T)0;
         }
     }
+}
+
+template <typename T, int CC, int MODE>
+__global__ void __launch_bounds__(kThreads) x_kernel(const XArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    x_body<T, CC, MODE>(a, blockIdx.x, smem_raw);
 }
 
 // ---- plan-time FP64 coefficient kernel (Algorithm 1, precompute lines) ----------

@@ -17,12 +17,11 @@ struct TileOf {
 };
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kThreads, 3) col2_kernel(const ColArgs<T> a) {
+__device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, unsigned char* smem_raw) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N>::E;
     using C = typename E::C;
     constexpr int LD = E::LD, G = E::G;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* red = buf + E::ROWS * LD;
     C* red2 = red + G * CC;
@@ -33,8 +32,8 @@ __global__ void __launch_bounds__(kThreads, 3) col2_kernel(const ColArgs<T> a) {
     const C* tw = static_cast<const C*>(ax.tw);
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
     for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);   // visible after the first barrier
-    const int xA = blockIdx.x * a.xw + c, xB = xA + a.bshift;
-    const long long other = blockIdx.y;
+    const int xA = bx * a.xw + c, xB = xA + a.bshift;
+    const long long other = by;
 
     {
         // all loads of this thread issued before any shared-memory store
@@ -120,16 +119,21 @@ __global__ void __launch_bounds__(kThreads, 3) col2_kernel(const ColArgs<T> a) {
             if (okB) qA[i * a.out_sAxis + a.out_offB] = v.y;
         });
     }
-    if (MODE == MODE_TD && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) a.clock->k += 1;
+    if (MODE == MODE_TD && bx == 0 && by == 0 && threadIdx.x == 0) a.clock->k += 1;
 }
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kThreads, 3) x2_kernel(const XArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, 3) col2_kernel(const ColArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    col2_body<T, N, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+template <typename T, int N, int MODE>
+__device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char* smem_raw) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N>::E;
     using C = typename E::C;
     constexpr int LD = E::LD, G = E::G;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* red = buf + E::ROWS * LD;
     C* red2 = red + G * CC;
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 3) x2_kernel(const XArgs<T> a) {
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
     for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);   // visible after the first barrier
     const int shiftB = (a.S == 2) ? 0 : CC;
-    const int r0 = blockIdx.x * (a.S == 2 ? CC : 2 * CC);
+    const int r0 = bx * (a.S == 2 ? CC : 2 * CC);
 
     // transposed load: warp w reads rows w, w + 8, ... ; lane l reads x = l, l + 32, ...
     {
@@ -223,6 +227,12 @@ __global__ void __launch_bounds__(kThreads, 3) x2_kernel(const XArgs<T> a) {
             }
         }
     }
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(kThreads, 3) x2_kernel(const XArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    x2_body<T, N, MODE>(a, blockIdx.x, smem_raw);
 }
 
 // ---- launch --------------------------------------------------------------------------

@@ -13,7 +13,7 @@ namespace sfrd {
 
 static thread_local std::string g_last_error;
 
-static int cuda_fail(cudaError_t e, const char* where) {
+int cuda_fail(cudaError_t e, const char* where) {
     g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return SFRD_ECUDA;
 }
@@ -102,7 +102,7 @@ static int unknowns(int bc, long long N) {
     return bc == SFRD_BC_PERIODIC ? (int)N : (bc == SFRD_BC_DIRICHLET ? (int)N - 1 : (int)N + 1);
 }
 
-static int create(Plan** out, const sfrd_grid* g, int bc, const double* alpha, const double* kappa, double dt,
+int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, const double* kappa, double dt,
                   int dtype, const sfrd_reaction* re) {
     if (!out || !g || !alpha || !kappa || !re) return SFRD_EINVAL;
     *out = nullptr;
@@ -303,7 +303,7 @@ static void drop_graph(Plan* p) {
     p->step_graph = nullptr;
 }
 
-static int bind(Plan* p, void* ws, size_t bytes, void* stream) {
+int bind_plan(Plan* p, void* ws, size_t bytes, void* stream) {
     if (!ws || bytes < p->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255u)) return SFRD_ENOWS;
     drop_graph(p);
     p->ws = static_cast<char*>(ws);
@@ -415,7 +415,7 @@ int sfrd_plan(sfrd_plan_t* out, const sfrd_grid* grid, int32_t bc, const double*
     if (!out) return SFRD_EINVAL;
     *out = nullptr;
     Plan* p = nullptr;
-    int rc = sfrd::create(&p, grid, bc, alpha, kappa, dt, dtype, reaction);
+    int rc = sfrd::create_plan(&p, grid, bc, alpha, kappa, dt, dtype, reaction);
     if (rc != SFRD_OK) return rc;
     sfrd_plan_s* h = new (std::nothrow) sfrd_plan_s();
     if (!h) {
@@ -454,7 +454,7 @@ int sfrd_get_info(sfrd_plan_t plan, sfrd_info* info) {
 
 int sfrd_bind(sfrd_plan_t plan, void* workspace, size_t bytes, void* stream) {
     if (!plan) return SFRD_EINVAL;
-    return sfrd::bind(&plan->p, workspace, bytes, stream);
+    return sfrd::bind_plan(&plan->p, workspace, bytes, stream);
 }
 
 int sfrd_load(sfrd_plan_t plan, const void* u0, double t0) {

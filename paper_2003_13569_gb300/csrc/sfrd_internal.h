@@ -202,4 +202,10 @@ cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s, long long k0 = 
 
 int kernels_per_step(const Plan& p);
 
+// Plan construction and binding shared by the single-instance and batched C ABI.
+int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, const double* kappa, double dt,
+                int dtype, const sfrd_reaction* re);
+int bind_plan(Plan* p, void* ws, size_t bytes, void* stream);
+int cuda_fail(cudaError_t e, const char* where);
+
 }  // namespace sfrd
