@@ -211,7 +211,7 @@ static void batch_tables(BatchPlan& b, std::vector<char>& host) {
 
 template <typename T>
 cudaError_t batch_prepare() {
-    const int m = v2::kMaxDynSmem2;
+    const int m = 192 * 1024;   // leaves room for the static shared arguments of the batched kernels
     void (*xs[])(const BatchX<T>*, const BatchItem*, int, double, int*) = {batch_x_kernel<T, MODE_REACT>};
     for (auto k : xs) SFRD_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m));
     void (*cs[])(const BatchC<T>*, const BatchItem*, int, int*) = {
