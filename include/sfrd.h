@@ -176,6 +176,25 @@ int sfrd_forward(sfrd_plan_t plan, const void* u, void* uhat);
  * (N for periodic, N/2 otherwise). */
 int sfrd_inverse(sfrd_plan_t plan, const void* uhat, void* u);
 
+/* Allocation-free form of sfrd_forward (no counterpart in the paper: an
+ * implementation service).  For callers that must not allocate device memory
+ * at all -- e.g. a component embedded in a host application that owns the GPU
+ * memory budget and forbids allocations after start-up, or a latency-critical
+ * loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree.
+ * The plan needs no workspace and no sfrd_bind: the scratch (one padded field
+ * of the plan plus its twiddle and permutation tables) lives in a fixed device
+ * array of 16 MiB that every GPU loading this library holds until exit.  u and
+ * uhat are caller-owned device fields [S][...] (same layout and result as
+ * sfrd_forward); stream is a cudaStream_t (NULL: legacy default stream).
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current).  Every call shares the array and leaves its
+ * contents behind; the call clears what must start at zero.  Calls that
+ * overlap on the GPU (other streams, other threads) race on the array, and the
+ * plan must not be used by another thread during the call.  Synchronises the
+ * stream.  Errors: SFRD_EUNSUPPORTED when the plan's scratch exceeds 16 MiB,
+ * SFRD_ECUDA, SFRD_EINVAL. */
+int sfrd_forward_noalloc(sfrd_plan_t plan, const void* u, void* uhat, void* stream);
+
 /* Copy coefficient array `which` (0 R13, 1 Q13, 2 phi, 3 phi1, 4 phi2, 5 phi3;
  * Algorithm 1) for every species into the dense device buffer out [S][...],
  * indexed like the spectral field (mode k per axis in eigenvalue order). */

@@ -30,7 +30,7 @@ REACTION = {"none": 0, "linear": 1, "fhn": 2, "gray_scott": 3, "schnakenberg": 4
             "gierer_meinhardt": 5, "huxley_mms": 6}
 COEFFICIENTS = ("R13", "Q13", "phi", "phi1", "phi2", "phi3")
 EXPORTS = ("sfrd_plan", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
-           "sfrd_store", "sfrd_run", "sfrd_step", "sfrd_run_host", "sfrd_forward", "sfrd_inverse",
+           "sfrd_store", "sfrd_run", "sfrd_step", "sfrd_run_host", "sfrd_forward", "sfrd_forward_noalloc", "sfrd_inverse",
            "sfrd_coefficients", "sfrd_profile_step", "sfrd_adjoint_workspace_bytes", "sfrd_run_checkpointed",
            "sfrd_adjoint", "sfrd_batch_plan", "sfrd_batch_workspace_bytes", "sfrd_batch_bind", "sfrd_batch_load",
            "sfrd_batch_advance", "sfrd_batch_store", "sfrd_batch_info", "sfrd_batch_destroy", "sfrd_destroy",
@@ -69,6 +69,7 @@ _lib.sfrd_step.argtypes = [_P, _P, _D]
 _lib.sfrd_run_host.argtypes = [_P, _P, _P, _D, ctypes.c_int64]
 _lib.sfrd_forward.argtypes = [_P, _P, _P]
 _lib.sfrd_inverse.argtypes = [_P, _P, _P]
+_lib.sfrd_forward_noalloc.argtypes = [_P, _P, _P, _P]
 _lib.sfrd_coefficients.argtypes = [_P, ctypes.c_int32, _P]
 _lib.sfrd_profile_step.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_int32)]

@@ -402,6 +402,10 @@ struct sfrd_plan_s {
     Plan p;
 };
 
+namespace sfrd {
+Plan* plan_of(sfrd_plan_t h) { return &h->p; }
+}  // namespace sfrd
+
 #define SFRD_CUDA_C(call)                                           \
     do {                                                            \
         cudaError_t e_ = (call);                                    \
