@@ -82,7 +82,7 @@ __device__ __forceinline__ void flush_sums(const double* acc, double* dst) {
 }
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kThreads, 3) adj_col_kernel(const ColArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE_TA>())) adj_col_kernel(const ColArgs<T> a) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N>::E;
     using C = typename E::C;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 3) adj_col_kernel(const ColArgs<T> a
 
 // Contiguous axis: out = T(J_f(state)^T T(in)), dL/dparams += sum_x w(x) (df/dp) . T(in).
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads, 3) adj_x_kernel(const XArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE_TA>())) adj_x_kernel(const XArgs<T> a) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N>::E;
     using C = typename E::C;

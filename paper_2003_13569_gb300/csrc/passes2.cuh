@@ -4,11 +4,20 @@
 // shared-memory FFT on the 2N extension.
 #pragma once
 
+#include <type_traits>
+
 #include "fft2.cuh"
 #include "reaction.cuh"
 
 namespace sfrd {
 namespace v2 {
+
+// Blocks per SM the register allocation is sized for: 64-80 registers per thread for
+// FP32 lines up to 256, 128 for longer lines and for FP64, 255 for FP64 at 512-1024.
+template <typename T, int N, int MODE>
+constexpr int min_blocks() {
+    return sizeof(T) == 8 ? (N >= 512 ? 1 : 2) : (N >= 512 ? 2 : ((MODE == MODE_PLAIN || MODE == MODE_REACT) ? 4 : 3));
+}
 
 template <typename T, int N>
 struct TileOf {
@@ -82,22 +91,26 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
                 const long long i = ix[h];
+                // read-only inputs through the non-coherent path so that they are not ordered
+                // behind this pass's stores (every element is read once, before its own update)
                 if (MODE == MODE_T0) {
                     a.U[i] = F[h];
                     s[h] = F[h];
                 } else if (MODE == MODE_TA || MODE == MODE_TB) {
+                    const T Q = __ldg(a.CQ + 2 * i), ph = __ldg(a.CQ + 2 * i + 1), u = __ldg(a.U + i);
                     if (MODE == MODE_TA) a.F1[i] = F[h]; else a.F2[i] = F[h];
-                    const T Q = a.CQ[2 * i], ph = a.CQ[2 * i + 1];
-                    s[h] = Q * a.U[i] + ph * F[h];
+                    s[h] = Q * u + ph * F[h];
                 } else if (MODE == MODE_TC) {
+                    const T Q = __ldg(a.CQ + 2 * i), ph = __ldg(a.CQ + 2 * i + 1);
+                    const T f1 = __ldg(a.F1 + i), u = __ldg(a.U + i);
                     a.F3[i] = F[h];
-                    const T Q = a.CQ[2 * i], ph = a.CQ[2 * i + 1];
-                    const T f1 = a.F1[i];
-                    const T ah = Q * a.U[i] + ph * f1;
+                    const T ah = Q * u + ph * f1;
                     s[h] = Q * ah + ph * ((T)2 * F[h] - f1);
                 } else {  // MODE_TD
-                    const T R = a.CR[4 * i], p1 = a.CR[4 * i + 1], p2 = a.CR[4 * i + 2], p3 = a.CR[4 * i + 3];
-                    const T un = R * a.U[i] + p1 * a.F1[i] + p2 * (a.F2[i] + a.F3[i]) + p3 * F[h];
+                    const T R = __ldg(a.CR + 4 * i), p1 = __ldg(a.CR + 4 * i + 1);
+                    const T p2 = __ldg(a.CR + 4 * i + 2), p3 = __ldg(a.CR + 4 * i + 3);
+                    const T u = __ldg(a.U + i), f1 = __ldg(a.F1 + i), f2 = __ldg(a.F2 + i), f3 = __ldg(a.F3 + i);
+                    const T un = R * u + p1 * f1 + p2 * (f2 + f3) + p3 * F[h];
                     if (a.F4) a.F4[i] = F[h];
                     a.U[i] = un;
                     s[h] = un;
@@ -123,7 +136,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
 }
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kThreads, 3) col2_kernel(const ColArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) col2_kernel(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     col2_body<T, N, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
@@ -184,25 +197,46 @@ __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char
         const double t = a.clock->t0 + ((double)a.clock->k + a.stage_frac) * a.tau;
         const int rA = r0 + c, rB = rA + shiftB;
         T* sv = a.save ? a.save + (long long)rA * a.out_pitch : nullptr;   // stage save (adjoint recomputation)
+        if (a.S == 2 && !sv) {
+            // two-species kinds: one loop per kind so that the reaction's switch is resolved at compile time
+            auto loop = [&](auto kind) {
 #pragma unroll 1
-        for (int i = g; i < n; i += G) {
-            const C v = buf[i * LD + c];
-            if (sv) {
-                if (rA < a.rows) sv[i] = v.x;
-                if (rB < a.rows) sv[a.out_offB + i] = v.y;
+                for (int i = g; i < n; i += G) {
+                    const C v = buf[i * LD + c];
+                    C f;
+                    react2k<T>(decltype(kind)::value, a.re, v.x, v.y, f.x, f.y);
+                    buf[i * LD + c] = f;
+                }
+            };
+            switch (a.re.kind) {
+                case SFRD_REACT_SCHNAKENBERG: loop(std::integral_constant<int, SFRD_REACT_SCHNAKENBERG>()); break;
+                case SFRD_REACT_GRAY_SCOTT: loop(std::integral_constant<int, SFRD_REACT_GRAY_SCOTT>()); break;
+                case SFRD_REACT_FHN: loop(std::integral_constant<int, SFRD_REACT_FHN>()); break;
+                case SFRD_REACT_GIERER_MEINHARDT: loop(std::integral_constant<int, SFRD_REACT_GIERER_MEINHARDT>()); break;
+                case SFRD_REACT_LINEAR: loop(std::integral_constant<int, SFRD_REACT_LINEAR>()); break;
+                default: loop(std::integral_constant<int, SFRD_REACT_NONE>()); break;
             }
-            C f;
-            if (a.S == 2) {
-                react2<T>(a.re, v.x, v.y, f.x, f.y);
-            } else {
-                const double x = ax.lo + (ax.node0 + i) * ax.h;
-                const int yA = rA % a.ny, yB = rB % a.ny;
-                const double ya = a.ay.lo + (a.ay.node0 + yA) * a.ay.h;
-                const double yb = a.ay.lo + (a.ay.node0 + yB) * a.ay.h;
-                f.x = react1<T>(a.re, v.x, x, ya, t);
-                f.y = react1<T>(a.re, v.y, x, yb, t);
+        } else {
+#pragma unroll 1
+            for (int i = g; i < n; i += G) {
+                const C v = buf[i * LD + c];
+                if (sv) {
+                    if (rA < a.rows) sv[i] = v.x;
+                    if (rB < a.rows) sv[a.out_offB + i] = v.y;
+                }
+                C f;
+                if (a.S == 2) {
+                    react2<T>(a.re, v.x, v.y, f.x, f.y);
+                } else {
+                    const double x = ax.lo + (ax.node0 + i) * ax.h;
+                    const int yA = rA % a.ny, yB = rB % a.ny;
+                    const double ya = a.ay.lo + (a.ay.node0 + yA) * a.ay.h;
+                    const double yb = a.ay.lo + (a.ay.node0 + yB) * a.ay.h;
+                    f.x = react1<T>(a.re, v.x, x, ya, t);
+                    f.y = react1<T>(a.re, v.y, x, yb, t);
+                }
+                buf[i * LD + c] = f;
             }
-            buf[i * LD + c] = f;
         }
         __syncthreads();
         E::forward(buf, red2, bc, tws, twstride, c, g);
@@ -230,7 +264,7 @@ __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char
 }
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(kThreads, 3) x2_kernel(const XArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) x2_kernel(const XArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     x2_body<T, N, MODE>(a, blockIdx.x, smem_raw);
 }
@@ -269,11 +303,13 @@ cudaError_t prepare2() {
                                       col2_kernel<T, N, MODE_TC>,    col2_kernel<T, N, MODE_TD>};
     for (auto k : ks) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
     }
     void (*xs[])(const XArgs<T>) = {x2_kernel<T, N, MODE_PLAIN>, x2_kernel<T, N, MODE_REACT>};
     for (auto k : xs) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -7,9 +7,11 @@ namespace sfrd {
 
 // ---- reaction terms (Section 5.2; parameters as documented in sfrd.h) -----------
 
+// `kind` is passed separately so that a caller can give a compile-time constant
+// and have the switch folded away.
 template <typename T>
-__device__ __forceinline__ void react2(const ReactDev& re, T u, T v, T& fu, T& fv) {
-    switch (re.kind) {
+__device__ __forceinline__ void react2k(int kind, const ReactDev& re, T u, T v, T& fu, T& fv) {
+    switch (kind) {
         case SFRD_REACT_FHN: {
             const T mu = (T)re.p[0], eps = (T)re.p[1], beta = (T)re.p[2], gam = (T)re.p[3], del = (T)re.p[4];
             fu = u * ((T)1 - u) * (u - mu) - v;
@@ -41,6 +43,11 @@ __device__ __forceinline__ void react2(const ReactDev& re, T u, T v, T& fu, T& f
             fu = 0;
             fv = 0;
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void react2(const ReactDev& re, T u, T v, T& fu, T& fv) {
+    react2k<T>(re.kind, re, u, v, fu, fv);
 }
 
 // Single-species terms; x, y are node coordinates, t the stage time.
