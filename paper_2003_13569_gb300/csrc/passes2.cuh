@@ -19,11 +19,6 @@ constexpr int min_blocks() {
     return sizeof(T) == 8 ? (N >= 512 ? 1 : 2) : (N >= 512 ? 2 : ((MODE == MODE_PLAIN || MODE == MODE_REACT) ? 4 : 3));
 }
 
-// Asks the memory system to bring [p, p + bytes) into L2 (bytes a multiple of 16, p 16-byte aligned).
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 template <typename T, int N>
 struct TileOf {
     static constexpr int CC = TileCC<T, N>::value;
@@ -49,30 +44,6 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     const int xA = bx * a.xw + c, xB = xA + a.bshift;
     const long long other = by;
 
-    if (MODE != MODE_PLAIN && MODE != MODE_T0 && c == 0) {
-        // the combination after the first transform reads rows of u^, stored spectra and
-        // coefficients at this tile's columns: start pulling them into L2 now
-        const int x0 = bx * a.xw;
-        const int span = (a.bshift ? 2 : 1) * CC;   // columns covered by lines A and B of this tile
-        const int cols = (x0 + span <= a.in_xlim ? span : a.in_xlim - x0);
-        const unsigned w1 = (unsigned)(cols * sizeof(T)) & ~15u;
-        const long long nsp = a.bshift ? 1 : 2;      // species rows per tile row
-        for (int i = g; i < n; i += G) {
-            for (long long h = 0; h < nsp; ++h) {
-                const long long e = other * a.in_sOther + (long long)i * a.in_sAxis + x0 + h * a.in_offB;
-                if (w1 == 0) continue;
-                prefetch_l2(a.U + e, w1);
-                if (MODE == MODE_TD) {
-                    prefetch_l2(a.CR + 4 * e, 4 * w1);
-                    prefetch_l2(a.F2 + e, w1);
-                    prefetch_l2(a.F3 + e, w1);
-                } else {
-                    prefetch_l2(a.CQ + 2 * e, 2 * w1);
-                }
-                if (MODE == MODE_TC || MODE == MODE_TD) prefetch_l2(a.F1 + e, w1);
-            }
-        }
-    }
     {
         // all loads of this thread issued before any shared-memory store
         constexpr int NL = (E::ROWS + G - 1) / G;
