@@ -265,8 +265,12 @@ struct Eng {
         s = t;
     }
 
-    template <class Sink>
-    static __device__ __forceinline__ void post(C* buf, C* red, const C* red2, int bc, int c, int g, Sink&& sink) {
+    // Emission in batches of B half-spectrum pairs: pre(slot, i) is called for every output i
+    // of a batch before sink(slot, i, value) is called for them, so that a caller can issue
+    // all global loads of a batch together (slot < 2B is a compile-time index).
+    template <int B, class Pre, class Sink>
+    static __device__ __forceinline__ void post_b(C* buf, C* red, const C* red2, int bc, int c, int g, Pre&& pre,
+                                                  Sink&& sink) {
         C ev[CH], od[CH];   // even-index outputs, running odd-index partial sums
         C run = czero<C>(), err = czero<C>();
         const int k0 = g * CH;
@@ -316,23 +320,56 @@ struct Eng {
             for (int q = 0; q < g; ++q) kadd(pre_sum, perr, red[q * CC + c]);
             pre_sum = csub(pre_sum, perr);
         }
-#pragma unroll
-        for (int t = 0; t < CH; ++t) {
+        // output q (0, 1) of pair t: index and value, or false when there is none
+        auto out_of = [&](int t, int q, int& i, C& v) -> bool {
             const int k = k0 + t;
-            if (k < H) {
-                if (bc == SFRD_BC_PERIODIC) {
-                    sink(k, ev[t]);
-                    if (k != 0) sink(N - k, od[t]);
-                } else if (bc == SFRD_BC_DIRICHLET) {
-                    if (k != 0) sink(2 * k - 1, ev[t]);
-                    sink(2 * k, cadd(pre_sum, od[t]));
-                } else {
-                    sink(2 * k, ev[t]);
-                    sink(2 * k + 1, cadd(pre_sum, od[t]));
+            if (k >= H) return false;
+            if (bc == SFRD_BC_PERIODIC) {
+                if (q == 0) { i = k; v = ev[t]; return true; }
+                if (k == 0) return false;
+                i = N - k; v = od[t]; return true;
+            }
+            if (bc == SFRD_BC_DIRICHLET) {
+                if (q == 0) {
+                    if (k == 0) return false;
+                    i = 2 * k - 1; v = ev[t]; return true;
+                }
+                i = 2 * k; v = cadd(pre_sum, od[t]); return true;
+            }
+            if (q == 0) { i = 2 * k; v = ev[t]; return true; }
+            i = 2 * k + 1; v = cadd(pre_sum, od[t]); return true;
+        };
+#pragma unroll
+        for (int t0 = 0; t0 < CH; t0 += B) {
+#pragma unroll
+            for (int t = t0; t < t0 + B && t < CH; ++t) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    int i;
+                    C v;
+                    if (out_of(t, q, i, v)) pre(2 * (t - t0) + q, i);
+                }
+            }
+#pragma unroll
+            for (int t = t0; t < t0 + B && t < CH; ++t) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    int i;
+                    C v;
+                    if (out_of(t, q, i, v)) sink(2 * (t - t0) + q, i, v);
                 }
             }
         }
-        if (bc != SFRD_BC_DIRICHLET && g == G - 1) sink(bc == SFRD_BC_PERIODIC ? H : N, nyq);
+        if (bc != SFRD_BC_DIRICHLET && g == G - 1) {
+            const int i = bc == SFRD_BC_PERIODIC ? H : N;
+            pre(0, i);
+            sink(0, i, nyq);
+        }
+    }
+
+    template <class Sink>
+    static __device__ __forceinline__ void post(C* buf, C* red, const C* red2, int bc, int c, int g, Sink&& sink) {
+        post_b<CH>(buf, red, red2, bc, c, g, [](int, int) {}, [&](int, int i, C v) { sink(i, v); });
     }
 };
 

@@ -16,7 +16,8 @@ namespace v2 {
 // FP32 lines up to 256, 128 for longer lines and for FP64, 255 for FP64 at 512-1024.
 template <typename T, int N, int MODE>
 constexpr int min_blocks() {
-    return sizeof(T) == 8 ? (N >= 512 ? 1 : 2) : (N >= 512 ? 2 : ((MODE == MODE_PLAIN || MODE == MODE_REACT) ? 4 : 3));
+    return sizeof(T) == 8 ? (N >= 512 ? 1 : 2)
+                          : (N >= 512 ? 2 : ((MODE == MODE_PLAIN || MODE == MODE_REACT) ? 4 : (MODE == MODE_TD ? 2 : 3)));
 }
 
 template <typename T, int N>
@@ -81,36 +82,61 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         const long long base = other * a.in_sOther + xA;
         const long long oB = a.in_offB;
         const T invC = (T)a.invC;
-        E::post(buf, red, red2, bc, c, g, [&](int k, C Fv) {
-            const long long iA = base + k * a.in_sAxis, iB = iA + oB;
-            const T F[2] = {Fv.x, Fv.y};
-            T s[2] = {0, 0};
-            const bool ok[2] = {okA, okB};
-            const long long ix[2] = {iA, iB};
+        // values read by the combination: batch-loaded (all loads of a batch before any use)
+        constexpr int NV = (MODE == MODE_TD) ? 8 : (MODE == MODE_TC ? 4 : (MODE == MODE_T0 ? 1 : 3));
+        constexpr int B = (MODE == MODE_TA || MODE == MODE_TB) ? 2 : 1;
+        T ld[2 * B][2][NV];
+        const bool ok[2] = {okA, okB};
+        auto pre = [&](int slot, int k) {
+            const long long iA = base + k * a.in_sAxis;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
-                const long long i = ix[h];
-                // read-only inputs through the non-coherent path so that they are not ordered
-                // behind this pass's stores (every element is read once, before its own update)
+                const long long i = iA + (h ? oB : 0);
+                // read-only inputs through the non-coherent path (every element is read once,
+                // before its own update)
+                if (MODE == MODE_TA || MODE == MODE_TB) {
+                    ld[slot][h][0] = __ldg(a.CQ + 2 * i);
+                    ld[slot][h][1] = __ldg(a.CQ + 2 * i + 1);
+                    ld[slot][h][2] = __ldg(a.U + i);
+                } else if (MODE == MODE_TC) {
+                    ld[slot][h][0] = __ldg(a.CQ + 2 * i);
+                    ld[slot][h][1] = __ldg(a.CQ + 2 * i + 1);
+                    ld[slot][h][2] = __ldg(a.U + i);
+                    ld[slot][h][3] = __ldg(a.F1 + i);
+                } else if (MODE == MODE_TD) {
+                    ld[slot][h][0] = __ldg(a.CR + 4 * i);
+                    ld[slot][h][1] = __ldg(a.CR + 4 * i + 1);
+                    ld[slot][h][2] = __ldg(a.CR + 4 * i + 2);
+                    ld[slot][h][3] = __ldg(a.CR + 4 * i + 3);
+                    ld[slot][h][4] = __ldg(a.U + i);
+                    ld[slot][h][5] = __ldg(a.F1 + i);
+                    ld[slot][h][6] = __ldg(a.F2 + i);
+                    ld[slot][h][7] = __ldg(a.F3 + i);
+                }
+            }
+        };
+        E::post_b<B>(buf, red, red2, bc, c, g, pre, [&](int slot, int k, C Fv) {
+            const long long iA = base + k * a.in_sAxis;
+            const T F[2] = {Fv.x, Fv.y};
+            T s[2] = {0, 0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!ok[h]) continue;
+                const long long i = iA + (h ? oB : 0);
+                const T* L = ld[slot][h];
                 if (MODE == MODE_T0) {
                     a.U[i] = F[h];
                     s[h] = F[h];
                 } else if (MODE == MODE_TA || MODE == MODE_TB) {
-                    const T Q = __ldg(a.CQ + 2 * i), ph = __ldg(a.CQ + 2 * i + 1), u = __ldg(a.U + i);
                     if (MODE == MODE_TA) a.F1[i] = F[h]; else a.F2[i] = F[h];
-                    s[h] = Q * u + ph * F[h];
+                    s[h] = L[0] * L[2] + L[1] * F[h];
                 } else if (MODE == MODE_TC) {
-                    const T Q = __ldg(a.CQ + 2 * i), ph = __ldg(a.CQ + 2 * i + 1);
-                    const T f1 = __ldg(a.F1 + i), u = __ldg(a.U + i);
                     a.F3[i] = F[h];
-                    const T ah = Q * u + ph * f1;
-                    s[h] = Q * ah + ph * ((T)2 * F[h] - f1);
+                    const T ah = L[0] * L[2] + L[1] * L[3];
+                    s[h] = L[0] * ah + L[1] * ((T)2 * F[h] - L[3]);
                 } else {  // MODE_TD
-                    const T R = __ldg(a.CR + 4 * i), p1 = __ldg(a.CR + 4 * i + 1);
-                    const T p2 = __ldg(a.CR + 4 * i + 2), p3 = __ldg(a.CR + 4 * i + 3);
-                    const T u = __ldg(a.U + i), f1 = __ldg(a.F1 + i), f2 = __ldg(a.F2 + i), f3 = __ldg(a.F3 + i);
-                    const T un = R * u + p1 * f1 + p2 * (f2 + f3) + p3 * F[h];
+                    const T un = L[0] * L[4] + L[1] * L[5] + L[2] * (L[6] + L[7]) + L[3] * F[h];
                     if (a.F4) a.F4[i] = F[h];
                     a.U[i] = un;
                     s[h] = un;
