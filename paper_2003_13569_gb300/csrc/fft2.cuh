@@ -251,20 +251,6 @@ struct Eng {
 
     // Z (natural) -> transform values; sink(i, value) is called for every unknown i
     // of this thread's output range after a barrier (so the sink may write V).
-    // Compensated (Kahan) accumulation s += d with running error e; used by the
-    // prefix sums of the odd-index outputs so that their rounding error does not
-    // grow with the number of terms.
-    static __device__ __forceinline__ void kadd(C& s, C& e, C d) {
-        C y, t;
-        y.x = d.x - e.x;
-        y.y = d.y - e.y;
-        t.x = s.x + y.x;
-        t.y = s.y + y.y;
-        e.x = (t.x - s.x) - y.x;
-        e.y = (t.y - s.y) - y.y;
-        s = t;
-    }
-
     // Emission in batches of B half-spectrum pairs: pre(slot, i) is called for every output i
     // of a batch before sink(slot, i, value) is called for them, so that a caller can issue
     // all global loads of a batch together (slot < 2B is a compile-time index).
@@ -272,7 +258,7 @@ struct Eng {
     static __device__ __forceinline__ void post_b(C* buf, C* red, const C* red2, int bc, int c, int g, Pre&& pre,
                                                   Sink&& sink) {
         C ev[CH], od[CH];   // even-index outputs, running odd-index partial sums
-        C run = czero<C>(), err = czero<C>();
+        C run = czero<C>();
         const int k0 = g * CH;
 #pragma unroll
         for (int t = 0; t < CH; ++t) {
@@ -292,8 +278,8 @@ struct Eng {
                     ev[t] = Ik;
                     C d = Rk;
                     if (k == 0) { d.x *= (T)0.5; d.y *= (T)0.5; }
-                    kadd(run, err, d);
-                    od[t] = csub(run, err);
+                    run = cadd(run, d);
+                    od[t] = run;
                 } else {
                     ev[t] = Rk;
                     C d = Ik;
@@ -302,8 +288,8 @@ struct Eng {
 #pragma unroll 4
                         for (int q = 0; q < G; ++q) d = cadd(d, red2[q * CC + c]);
                     }
-                    kadd(run, err, d);
-                    od[t] = csub(run, err);
+                    run = cadd(run, d);
+                    od[t] = run;
                 }
             }
         }
@@ -312,13 +298,11 @@ struct Eng {
             const C zh = buf[H * LD + c];     // k = N/2: R = Re, I = 0 for both lines
             nyq = zh;
         }
-        if (bc != SFRD_BC_PERIODIC) red[g * CC + c] = csub(run, err);
+        if (bc != SFRD_BC_PERIODIC) red[g * CC + c] = run;
         __syncthreads();   // all reads of Z done: the buffer becomes V
         C pre_sum = czero<C>();
         if (bc != SFRD_BC_PERIODIC) {
-            C perr = czero<C>();
-            for (int q = 0; q < g; ++q) kadd(pre_sum, perr, red[q * CC + c]);
-            pre_sum = csub(pre_sum, perr);
+            for (int q = 0; q < g; ++q) pre_sum = cadd(pre_sum, red[q * CC + c]);
         }
         // output q (0, 1) of pair t: index and value, or false when there is none
         auto out_of = [&](int t, int q, int& i, C& v) -> bool {

@@ -17,7 +17,7 @@ namespace v2 {
 template <typename T, int N, int MODE>
 constexpr int min_blocks() {
     return sizeof(T) == 8 ? (N >= 512 ? 1 : 2)
-                          : (N >= 512 ? 2 : ((MODE == MODE_PLAIN || MODE == MODE_REACT) ? 4 : (MODE == MODE_TD ? 2 : 3)));
+                          : (N >= 512 ? 2 : ((MODE == MODE_PLAIN || MODE == MODE_REACT) ? 4 : 3));
 }
 
 template <typename T, int N>
@@ -83,7 +83,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         const long long oB = a.in_offB;
         const T invC = (T)a.invC;
         // values read by the combination: batch-loaded (all loads of a batch before any use)
-        constexpr int NV = (MODE == MODE_TD) ? 8 : (MODE == MODE_TC ? 4 : (MODE == MODE_T0 ? 1 : 3));
+        constexpr int NV = (MODE == MODE_TD || MODE == MODE_TC) ? 4 : (MODE == MODE_T0 ? 1 : 3);
         constexpr int B = (MODE == MODE_TA || MODE == MODE_TB) ? 2 : 1;
         T ld[2 * B][2][NV];
         const bool ok[2] = {okA, okB};
@@ -104,15 +104,11 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                     ld[slot][h][1] = __ldg(a.CQ + 2 * i + 1);
                     ld[slot][h][2] = __ldg(a.U + i);
                     ld[slot][h][3] = __ldg(a.F1 + i);
-                } else if (MODE == MODE_TD) {
-                    ld[slot][h][0] = __ldg(a.CR + 4 * i);
-                    ld[slot][h][1] = __ldg(a.CR + 4 * i + 1);
-                    ld[slot][h][2] = __ldg(a.CR + 4 * i + 2);
-                    ld[slot][h][3] = __ldg(a.CR + 4 * i + 3);
-                    ld[slot][h][4] = __ldg(a.U + i);
-                    ld[slot][h][5] = __ldg(a.F1 + i);
-                    ld[slot][h][6] = __ldg(a.F2 + i);
-                    ld[slot][h][7] = __ldg(a.F3 + i);
+                } else if (MODE == MODE_TD) {   // the coefficient quads are read in the sink
+                    ld[slot][h][0] = __ldg(a.U + i);
+                    ld[slot][h][1] = __ldg(a.F1 + i);
+                    ld[slot][h][2] = __ldg(a.F2 + i);
+                    ld[slot][h][3] = __ldg(a.F3 + i);
                 }
             }
         };
@@ -136,7 +132,9 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                     const T ah = L[0] * L[2] + L[1] * L[3];
                     s[h] = L[0] * ah + L[1] * ((T)2 * F[h] - L[3]);
                 } else {  // MODE_TD
-                    const T un = L[0] * L[4] + L[1] * L[5] + L[2] * (L[6] + L[7]) + L[3] * F[h];
+                    const T R = __ldg(a.CR + 4 * i), p1 = __ldg(a.CR + 4 * i + 1);
+                    const T p2 = __ldg(a.CR + 4 * i + 2), p3 = __ldg(a.CR + 4 * i + 3);
+                    const T un = R * L[0] + p1 * L[1] + p2 * (L[2] + L[3]) + p3 * F[h];
                     if (a.F4) a.F4[i] = F[h];
                     a.U[i] = un;
                     s[h] = un;
