@@ -161,8 +161,11 @@ template <> struct Split<1024> { static constexpr int R1 = 32, R2 = 32; };
 // Columns per tile for a power-of-two axis length.
 template <typename T, int N> struct TileCC { static constexpr int value = cc_for(sizeof(T) == 8, N); };
 
-template <typename T, int N, int CC>
+// BCT: the boundary condition as a compile-time constant (SFRD_BC_*), or -1 when it is
+// taken from the runtime argument.
+template <typename T, int N, int CC, int BCT = -1>
 struct Eng {
+    static __device__ __forceinline__ int bcv(int bc) { return BCT >= 0 ? BCT : bc; }
     using C = typename Cx<T>::type;
     static constexpr int G = kThreads / CC;
     static constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2;
@@ -178,7 +181,8 @@ struct Eng {
     }
 
     // Pre-processed input z_j of the packed DFT, read from the value buffer.
-    static __device__ __forceinline__ C pre(const C* V, int bc, int j, int c, const C* tws, C& anchor) {
+    static __device__ __forceinline__ C pre(const C* V, int bc_, int j, int c, const C* tws, C& anchor) {
+        const int bc = bcv(bc_);
         if (bc == SFRD_BC_PERIODIC) return V[j * LD + c];
         const C w = tws[j];               // (cos(j pi/N), -sin(j pi/N))
         const T s = -w.y;
@@ -208,8 +212,10 @@ struct Eng {
     // Entry: V complete (after a barrier).  Exit: Z complete (after a barrier).
     // red2[g][c] receives this thread's part of the Neumann anchor.
     // tws: the axis table in shared memory, omega_{N*twstride}^m (twstride = 1 periodic, 2 otherwise).
-    static __device__ __forceinline__ void forward(C* buf, C* red2, int bc, const C* tws, int twstride, int c,
+    static __device__ __forceinline__ void forward(C* buf, C* red2, int bc_, const C* tws, int twstride_, int c,
                                                    int g) {
+        const int bc = bcv(bc_);
+        const int twstride = BCT < 0 ? twstride_ : (BCT == SFRD_BC_PERIODIC ? 1 : 2);
         C a[NO1][R1];
         C anchor = czero<C>();
 #pragma unroll
@@ -255,8 +261,9 @@ struct Eng {
     // of a batch before sink(slot, i, value) is called for them, so that a caller can issue
     // all global loads of a batch together (slot < 2B is a compile-time index).
     template <int B, class Pre, class Sink>
-    static __device__ __forceinline__ void post_b(C* buf, C* red, const C* red2, int bc, int c, int g, Pre&& pre,
+    static __device__ __forceinline__ void post_b(C* buf, C* red, const C* red2, int bc_, int c, int g, Pre&& pre,
                                                   Sink&& sink) {
+        const int bc = bcv(bc_);
         C ev[CH], od[CH];   // even-index outputs, running odd-index partial sums
         C run = czero<C>();
         const int k0 = g * CH;

@@ -20,16 +20,19 @@ constexpr int min_blocks() {
                           : (N >= 512 ? 2 : ((MODE == MODE_PLAIN || MODE == MODE_REACT) ? 4 : 3));
 }
 
-template <typename T, int N>
+template <typename T, int N, int BCT = -1>
 struct TileOf {
     static constexpr int CC = TileCC<T, N>::value;
-    using E = Eng<T, N, CC>;
+    using E = Eng<T, N, CC, BCT>;
 };
 
-template <typename T, int N, int MODE>
+// Lengths whose passes are also compiled with the boundary condition fixed at compile time.
+template <typename T, int N> struct BcSpecialised { static constexpr bool value = sizeof(T) == 4 && N == 256; };
+
+template <typename T, int N, int MODE, int BCT = -1>
 __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, unsigned char* smem_raw) {
     constexpr int CC = TileOf<T, N>::CC;
-    using E = typename TileOf<T, N>::E;
+    using E = typename TileOf<T, N, BCT>::E;
     using C = typename E::C;
     constexpr int LD = E::LD, G = E::G;
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -159,16 +162,16 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     if (MODE == MODE_TD && bx == 0 && by == 0 && threadIdx.x == 0) a.clock->k += 1;
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int BCT = -1>
 __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) col2_kernel(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    col2_body<T, N, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);
+    col2_body<T, N, MODE, BCT>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int BCT = -1>
 __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char* smem_raw) {
     constexpr int CC = TileOf<T, N>::CC;
-    using E = typename TileOf<T, N>::E;
+    using E = typename TileOf<T, N, BCT>::E;
     using C = typename E::C;
     constexpr int LD = E::LD, G = E::G;
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -287,50 +290,51 @@ __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char
     }
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int BCT = -1>
 __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) x2_kernel(const XArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    x2_body<T, N, MODE>(a, blockIdx.x, smem_raw);
+    x2_body<T, N, MODE, BCT>(a, blockIdx.x, smem_raw);
 }
 
 // ---- launch --------------------------------------------------------------------------
 
-template <typename T, int N>
-cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+template <typename T, int N, int BCT>
+cudaError_t col2_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
     const size_t smem = TileOf<T, N>::E::smem_bytes();
     void (*k)(const ColArgs<T>) = nullptr;
     switch (mode) {
-        case MODE_PLAIN: k = col2_kernel<T, N, MODE_PLAIN>; break;
-        case MODE_T0: k = col2_kernel<T, N, MODE_T0>; break;
-        case MODE_TA: k = col2_kernel<T, N, MODE_TA>; break;
-        case MODE_TB: k = col2_kernel<T, N, MODE_TB>; break;
-        case MODE_TC: k = col2_kernel<T, N, MODE_TC>; break;
-        default: k = col2_kernel<T, N, MODE_TD>; break;
+        case MODE_PLAIN: k = col2_kernel<T, N, MODE_PLAIN, BCT>; break;
+        case MODE_T0: k = col2_kernel<T, N, MODE_T0, BCT>; break;
+        case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT>; break;
+        case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT>; break;
+        case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT>; break;
+        default: k = col2_kernel<T, N, MODE_TD, BCT>; break;
     }
     k<<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int N>
-cudaError_t x2_launch(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+template <typename T, int N, int BCT>
+cudaError_t x2_launch_bc(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
     const size_t smem = TileOf<T, N>::E::smem_bytes();
-    void (*k)(const XArgs<T>) = mode == MODE_REACT ? x2_kernel<T, N, MODE_REACT> : x2_kernel<T, N, MODE_PLAIN>;
+    void (*k)(const XArgs<T>) =
+        mode == MODE_REACT ? x2_kernel<T, N, MODE_REACT, BCT> : x2_kernel<T, N, MODE_PLAIN, BCT>;
     k<<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int N>
-cudaError_t prepare2() {
+template <typename T, int N, int BCT>
+cudaError_t prepare2_bc() {
     const int m = kMaxDynSmem2;
-    void (*ks[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_PLAIN>, col2_kernel<T, N, MODE_T0>,
-                                      col2_kernel<T, N, MODE_TA>,    col2_kernel<T, N, MODE_TB>,
-                                      col2_kernel<T, N, MODE_TC>,    col2_kernel<T, N, MODE_TD>};
+    void (*ks[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_PLAIN, BCT>, col2_kernel<T, N, MODE_T0, BCT>,
+                                      col2_kernel<T, N, MODE_TA, BCT>,    col2_kernel<T, N, MODE_TB, BCT>,
+                                      col2_kernel<T, N, MODE_TC, BCT>,    col2_kernel<T, N, MODE_TD, BCT>};
     for (auto k : ks) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
     }
-    void (*xs[])(const XArgs<T>) = {x2_kernel<T, N, MODE_PLAIN>, x2_kernel<T, N, MODE_REACT>};
+    void (*xs[])(const XArgs<T>) = {x2_kernel<T, N, MODE_PLAIN, BCT>, x2_kernel<T, N, MODE_REACT, BCT>};
     for (auto k : xs) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -339,10 +343,56 @@ cudaError_t prepare2() {
     return cudaSuccess;
 }
 
+// Per-boundary-condition variants (translation units of their own for the specialised lengths).
+template <typename T, int N, int BCT> cudaError_t col2_launch_bc(const ColArgs<T>&, int, dim3, cudaStream_t);
+template <typename T, int N, int BCT> cudaError_t x2_launch_bc(const XArgs<T>&, int, dim3, cudaStream_t);
+template <typename T, int N, int BCT> cudaError_t prepare2_bc();
+
+template <typename T, int N>
+cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+    if (BcSpecialised<T, N>::value) {
+        switch (a.ax.bc) {
+            case SFRD_BC_PERIODIC: return col2_launch_bc<T, N, SFRD_BC_PERIODIC>(a, mode, grid, s);
+            case SFRD_BC_DIRICHLET: return col2_launch_bc<T, N, SFRD_BC_DIRICHLET>(a, mode, grid, s);
+            default: return col2_launch_bc<T, N, SFRD_BC_NEUMANN>(a, mode, grid, s);
+        }
+    }
+    return col2_launch_bc<T, N, -1>(a, mode, grid, s);
+}
+
+template <typename T, int N>
+cudaError_t x2_launch(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+    if (BcSpecialised<T, N>::value) {
+        switch (a.ax.bc) {
+            case SFRD_BC_PERIODIC: return x2_launch_bc<T, N, SFRD_BC_PERIODIC>(a, mode, grid, s);
+            case SFRD_BC_DIRICHLET: return x2_launch_bc<T, N, SFRD_BC_DIRICHLET>(a, mode, grid, s);
+            default: return x2_launch_bc<T, N, SFRD_BC_NEUMANN>(a, mode, grid, s);
+        }
+    }
+    return x2_launch_bc<T, N, -1>(a, mode, grid, s);
+}
+
+template <typename T, int N>
+cudaError_t prepare2() {
+    if (BcSpecialised<T, N>::value) {
+        cudaError_t e = prepare2_bc<T, N, SFRD_BC_PERIODIC>();
+        if (e == cudaSuccess) e = prepare2_bc<T, N, SFRD_BC_DIRICHLET>();
+        if (e == cudaSuccess) e = prepare2_bc<T, N, SFRD_BC_NEUMANN>();
+        if (e != cudaSuccess) return e;
+    }
+    return prepare2_bc<T, N, -1>();
+}
+
 #define SFRD_V2_INSTANTIATE(T, N)                                                                  \
     template cudaError_t col2_launch<T, N>(const ColArgs<T>&, int, dim3, cudaStream_t);           \
     template cudaError_t x2_launch<T, N>(const XArgs<T>&, int, dim3, cudaStream_t);               \
-    template cudaError_t prepare2<T, N>();
+    template cudaError_t prepare2<T, N>();                                                        \
+    SFRD_V2_INSTANTIATE_BC(T, N, -1)
+
+#define SFRD_V2_INSTANTIATE_BC(T, N, BCT)                                                          \
+    template cudaError_t col2_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t);   \
+    template cudaError_t x2_launch_bc<T, N, BCT>(const XArgs<T>&, int, dim3, cudaStream_t);       \
+    template cudaError_t prepare2_bc<T, N, BCT>();
 
 }  // namespace v2
 }  // namespace sfrd
