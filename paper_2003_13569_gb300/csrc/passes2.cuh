@@ -29,6 +29,13 @@ struct TileOf {
 // Lengths whose passes are also compiled with the boundary condition fixed at compile time.
 template <typename T, int N> struct BcSpecialised { static constexpr bool value = sizeof(T) == 4 && N == 256; };
 
+// Unknowns along an axis of N intervals: N (periodic), N - 1 (Dirichlet), N + 1 (Neumann); taken
+// from the runtime axis descriptor when the boundary condition is not fixed at compile time.
+template <int N, int BCT>
+__device__ __forceinline__ int unknowns(int n_runtime) {
+    return BCT == SFRD_BC_PERIODIC ? N : (BCT == SFRD_BC_DIRICHLET ? N - 1 : (BCT == SFRD_BC_NEUMANN ? N + 1 : n_runtime));
+}
+
 template <typename T, int N, int MODE, int BCT = -1>
 __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, unsigned char* smem_raw) {
     constexpr int CC = TileOf<T, N>::CC;
@@ -39,9 +46,10 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     C* red = buf + E::ROWS * LD;
     C* red2 = red + G * CC;
     C* tws = red2 + G * CC;
+    if (MODE == MODE_PLAIN || MODE == MODE_TD) __builtin_assume(threadIdx.x < kThreads);
     const int tid = threadIdx.x, c = tid % CC, g = tid / CC;
     const AxisDev& ax = a.ax;
-    const int n = ax.n, bc = ax.bc;
+    const int n = unknowns<N, BCT>(ax.n), bc = ax.bc;
     const C* tw = static_cast<const C*>(ax.tw);
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
     for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);   // visible after the first barrier
@@ -86,7 +94,8 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         const long long oB = a.in_offB;
         const T invC = (T)a.invC;
         // values read by the combination: batch-loaded (all loads of a batch before any use)
-        constexpr int NV = (MODE == MODE_TD || MODE == MODE_TC) ? 4 : (MODE == MODE_T0 ? 1 : 3);
+        using V2 = typename Cx<T>::type;                                    // (Q13, phi) pair
+        constexpr int NV = MODE == MODE_TD ? 8 : (MODE == MODE_TC ? 4 : (MODE == MODE_T0 ? 1 : 3));
         constexpr int B = (MODE == MODE_TA || MODE == MODE_TB) ? 2 : 1;
         T ld[2 * B][2][NV];
         const bool ok[2] = {okA, okB};
@@ -97,17 +106,28 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                 if (!ok[h]) continue;
                 const long long i = iA + (h ? oB : 0);
                 // read-only inputs through the non-coherent path (every element is read once,
-                // before its own update)
-                if (MODE == MODE_TA || MODE == MODE_TB) {
-                    ld[slot][h][0] = __ldg(a.CQ + 2 * i);
-                    ld[slot][h][1] = __ldg(a.CQ + 2 * i + 1);
+                // before its own update); coefficient pairs and quads as single vector loads
+                if (MODE == MODE_TA || MODE == MODE_TB || MODE == MODE_TC) {
+                    const V2 q = __ldg(reinterpret_cast<const V2*>(a.CQ) + i);
+                    ld[slot][h][0] = q.x;
+                    ld[slot][h][1] = q.y;
                     ld[slot][h][2] = __ldg(a.U + i);
-                } else if (MODE == MODE_TC) {
-                    ld[slot][h][0] = __ldg(a.CQ + 2 * i);
-                    ld[slot][h][1] = __ldg(a.CQ + 2 * i + 1);
-                    ld[slot][h][2] = __ldg(a.U + i);
-                    ld[slot][h][3] = __ldg(a.F1 + i);
-                } else if (MODE == MODE_TD) {   // the coefficient quads are read in the sink
+                    if (MODE == MODE_TC) ld[slot][h][3] = __ldg(a.F1 + i);
+                } else if (MODE == MODE_TD) {
+                    if (sizeof(T) == 4) {
+                        const float4 r = __ldg(reinterpret_cast<const float4*>(a.CR) + i);
+                        ld[slot][h][4] = (T)r.x;
+                        ld[slot][h][5] = (T)r.y;
+                        ld[slot][h][6] = (T)r.z;
+                        ld[slot][h][7] = (T)r.w;
+                    } else {
+                        const double2 r0 = __ldg(reinterpret_cast<const double2*>(a.CR) + 2 * i);
+                        const double2 r1 = __ldg(reinterpret_cast<const double2*>(a.CR) + 2 * i + 1);
+                        ld[slot][h][4] = (T)r0.x;
+                        ld[slot][h][5] = (T)r0.y;
+                        ld[slot][h][6] = (T)r1.x;
+                        ld[slot][h][7] = (T)r1.y;
+                    }
                     ld[slot][h][0] = __ldg(a.U + i);
                     ld[slot][h][1] = __ldg(a.F1 + i);
                     ld[slot][h][2] = __ldg(a.F2 + i);
@@ -134,10 +154,8 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                     a.F3[i] = F[h];
                     const T ah = L[0] * L[2] + L[1] * L[3];
                     s[h] = L[0] * ah + L[1] * ((T)2 * F[h] - L[3]);
-                } else {  // MODE_TD
-                    const T R = __ldg(a.CR + 4 * i), p1 = __ldg(a.CR + 4 * i + 1);
-                    const T p2 = __ldg(a.CR + 4 * i + 2), p3 = __ldg(a.CR + 4 * i + 3);
-                    const T un = R * L[0] + p1 * L[1] + p2 * (L[2] + L[3]) + p3 * F[h];
+                } else {  // MODE_TD: U <- R U + phi1 F1 + phi2 (F2 + F3) + phi3 F4
+                    const T un = L[4] * L[0] + L[5] * L[1] + L[6] * (L[2] + L[3]) + L[7] * F[h];
                     if (a.F4) a.F4[i] = F[h];
                     a.U[i] = un;
                     s[h] = un;
@@ -178,9 +196,10 @@ __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char
     C* red = buf + E::ROWS * LD;
     C* red2 = red + G * CC;
     C* tws = red2 + G * CC;
+    __builtin_assume(threadIdx.x < kThreads);
     const int tid = threadIdx.x, c = tid % CC, g = tid / CC;
     const AxisDev& ax = a.ax;
-    const int n = ax.n, bc = ax.bc;
+    const int n = unknowns<N, BCT>(ax.n), bc = ax.bc;
     const C* tw = static_cast<const C*>(ax.tw);
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
     for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);   // visible after the first barrier
