@@ -48,7 +48,8 @@ extern "C" {
 #define SFRD_OK            0
 #define SFRD_EINVAL       -1  /* bad argument: alpha not in (1,2], kappa < 0, dt <= 0, N < 2, ... */
 #define SFRD_EUNSUPPORTED -2  /* valid problem outside what this build handles (length not
-                                 {2,3,5}-smooth, FFT length > 1024, dim not 2 or 3, ...) */
+                                 {2,3,5}-smooth, FFT length > 1024, dim not 2 or 3, a field
+                                 array of 2^32 elements or more, ...) */
 #define SFRD_ENOWS        -3  /* workspace missing, too small or not bound */
 #define SFRD_ECUDA        -4  /* a CUDA runtime call failed; see sfrd_last_error() */
 #define SFRD_ENONFINITE   -5  /* a non-finite value was detected in the state */

@@ -54,19 +54,25 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
     for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);   // visible after the first barrier
     const int xA = bx * a.xw + c, xB = xA + a.bshift;
-    const long long other = by;
+    // Element indices: one 64-bit tile origin per thread, then 32-bit offsets (every array of the
+    // pass holds fewer than 2^32 elements; checked when the plan is made).
+    const size_t org_in = (size_t)by * (size_t)a.in_sOther + (size_t)xA;
+    const size_t org_out = (size_t)by * (size_t)a.out_sOther + (size_t)xA;
+    const unsigned s_in = (unsigned)a.in_sAxis, s_out = (unsigned)a.out_sAxis;
 
     {
         // all loads of this thread issued before any shared-memory store
         constexpr int NL = (E::ROWS + G - 1) / G;
         const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
-        const T* pA = a.in + other * a.in_sOther + xA;
+        const T* pA = a.in + org_in;
+        const unsigned oB = (unsigned)a.in_offB;
         C z[NL];
 #pragma unroll
         for (int t = 0; t < NL; ++t) {
             const int i = g + t * G;
-            z[t].x = (okA && i < n) ? pA[i * a.in_sAxis] : (T)0;
-            z[t].y = (okB && i < n) ? pA[i * a.in_sAxis + a.in_offB] : (T)0;
+            const unsigned o = (unsigned)i * s_in;
+            z[t].x = (okA && i < n) ? pA[o] : (T)0;
+            z[t].y = (okB && i < n) ? pA[o + oB] : (T)0;
         }
 #pragma unroll
         for (int t = 0; t < NL; ++t) {
@@ -79,19 +85,20 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
 
     if (MODE == MODE_PLAIN) {
         const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
-        T* qA = a.out + other * a.out_sOther + xA;
+        T* qA = a.out + org_out;
+        const unsigned oB = (unsigned)a.out_offB;
         const T sc = (T)a.scale;
         E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
-            if (okA) qA[i * a.out_sAxis] = v.x * sc;
-            if (okB) qA[i * a.out_sAxis + a.out_offB] = v.y * sc;
+            const unsigned o = (unsigned)i * s_out;
+            if (okA) qA[o] = v.x * sc;
+            if (okB) qA[o + oB] = v.y * sc;
         });
         return;
     }
 
     {
         const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
-        const long long base = other * a.in_sOther + xA;
-        const long long oB = a.in_offB;
+        const unsigned e0 = (unsigned)org_in, eoB = (unsigned)a.in_offB;
         const T invC = (T)a.invC;
         // values read by the combination: batch-loaded (all loads of a batch before any use)
         using V2 = typename Cx<T>::type;                                    // (Q13, phi) pair
@@ -100,11 +107,11 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         T ld[2 * B][2][NV];
         const bool ok[2] = {okA, okB};
         auto pre = [&](int slot, int k) {
-            const long long iA = base + k * a.in_sAxis;
+            const unsigned eA = e0 + (unsigned)k * s_in;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
-                const long long i = iA + (h ? oB : 0);
+                const unsigned i = eA + (h ? eoB : 0u);
                 // read-only inputs through the non-coherent path (every element is read once,
                 // before its own update); coefficient pairs and quads as single vector loads
                 if (MODE == MODE_TA || MODE == MODE_TB || MODE == MODE_TC) {
@@ -121,8 +128,9 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                         ld[slot][h][6] = (T)r.z;
                         ld[slot][h][7] = (T)r.w;
                     } else {
-                        const double2 r0 = __ldg(reinterpret_cast<const double2*>(a.CR) + 2 * i);
-                        const double2 r1 = __ldg(reinterpret_cast<const double2*>(a.CR) + 2 * i + 1);
+                        const double2* cr = reinterpret_cast<const double2*>(a.CR) + 2 * (size_t)i;
+                        const double2 r0 = __ldg(cr);
+                        const double2 r1 = __ldg(cr + 1);
                         ld[slot][h][4] = (T)r0.x;
                         ld[slot][h][5] = (T)r0.y;
                         ld[slot][h][6] = (T)r1.x;
@@ -135,14 +143,15 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                 }
             }
         };
+        T* const F4 = a.F4;
         E::post_b<B>(buf, red, red2, bc, c, g, pre, [&](int slot, int k, C Fv) {
-            const long long iA = base + k * a.in_sAxis;
+            const unsigned eA = e0 + (unsigned)k * s_in;
             const T F[2] = {Fv.x, Fv.y};
             T s[2] = {0, 0};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
-                const long long i = iA + (h ? oB : 0);
+                const unsigned i = eA + (h ? eoB : 0u);
                 const T* L = ld[slot][h];
                 if (MODE == MODE_T0) {
                     a.U[i] = F[h];
@@ -156,7 +165,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                     s[h] = L[0] * ah + L[1] * ((T)2 * F[h] - L[3]);
                 } else {  // MODE_TD: U <- R U + phi1 F1 + phi2 (F2 + F3) + phi3 F4
                     const T un = L[4] * L[0] + L[5] * L[1] + L[6] * (L[2] + L[3]) + L[7] * F[h];
-                    if (a.F4) a.F4[i] = F[h];
+                    if (F4) F4[i] = F[h];
                     a.U[i] = un;
                     s[h] = un;
                 }
@@ -171,10 +180,12 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     E::forward(buf, red2, bc, tws, twstride, c, g);
     {
         const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
-        T* qA = a.out + other * a.out_sOther + xA;
+        T* qA = a.out + org_out;
+        const unsigned oB = (unsigned)a.out_offB;
         E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
-            if (okA) qA[i * a.out_sAxis] = v.x;
-            if (okB) qA[i * a.out_sAxis + a.out_offB] = v.y;
+            const unsigned o = (unsigned)i * s_out;
+            if (okA) qA[o] = v.x;
+            if (okB) qA[o + oB] = v.y;
         });
     }
     if (MODE == MODE_TD && bx == 0 && by == 0 && threadIdx.x == 0) a.clock->k += 1;
@@ -246,7 +257,7 @@ __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char
         if (a.S == 2 && !sv) {
             // two-species kinds: one loop per kind so that the reaction's switch is resolved at compile time
             auto loop = [&](auto kind) {
-#pragma unroll 1
+#pragma unroll 4
                 for (int i = g; i < n; i += G) {
                     const C v = buf[i * LD + c];
                     C f;

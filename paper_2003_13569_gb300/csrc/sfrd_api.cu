@@ -183,6 +183,11 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
     p->pitch = (p->n[0] + 3) / 4 * 4;
     p->plane = (long long)p->n[2] * p->n[1] * p->pitch;
     p->dense = (long long)p->n[2] * p->n[1] * p->n[0];
+    // the passes index within one array (S planes) with 32-bit element offsets
+    if ((unsigned long long)S * (unsigned long long)p->plane >= (1ull << 32)) {
+        delete p;
+        return SFRD_EUNSUPPORTED;
+    }
 
     // reaction parameters (host-side constants of the manufactured source)
     p->re.kind = re->kind;
