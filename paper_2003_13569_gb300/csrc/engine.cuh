@@ -37,6 +37,26 @@ template <typename C> __device__ __forceinline__ C mul_mi(C a) { C r; r.x = a.y;
 template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
 template <typename C> __device__ __forceinline__ C cneg(C a) { C r; r.x = -a.x; r.y = -a.y; return r; }
 template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
+// a * s + b for a real s
+template <typename C, typename T> __device__ __forceinline__ C cfma(C a, T s, C b) {
+    C r; r.x = a.x * s + b.x; r.y = a.y * s + b.y; return r;
+}
+
+// FP32 complex values use the paired single-precision instructions of sm_100 and later
+// (both halves of a 64-bit register pair in one instruction, each rounded as the scalar
+// operation would be).
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(rd));
+    return r;
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+__device__ __forceinline__ float2 cfma(float2 a, float s, float2 b) { return __ffma2_rn(a, make_float2(s, s), b); }
 
 template <typename C> __device__ __forceinline__ C ldtw(const C* tw, int i) { return __ldg(tw + i); }
 

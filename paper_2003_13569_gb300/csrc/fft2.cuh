@@ -189,23 +189,13 @@ struct Eng {
         if (bc == SFRD_BC_DIRICHLET) {
             if (j == 0) return czero<C>();
             const C xj = V[(j - 1) * LD + c], xm = V[(N - j - 1) * LD + c];
-            C z;
-            z.x = s * (xj.x + xm.x) + (T)0.5 * (xj.x - xm.x);
-            z.y = s * (xj.y + xm.y) + (T)0.5 * (xj.y - xm.y);
-            return z;
+            return cfma(cadd(xj, xm), s, cscale(csub(xj, xm), (T)0.5));
         }
         const C xj = V[j * LD + c], xm = V[(N - j) * LD + c];
-        if (j == 0) {
-            anchor.x += (T)0.5 * (xj.x - xm.x);
-            anchor.y += (T)0.5 * (xj.y - xm.y);
-        } else {
-            anchor.x += xj.x * w.x;
-            anchor.y += xj.y * w.x;
-        }
-        C z;
-        z.x = (T)0.5 * (xj.x + xm.x) - s * (xj.x - xm.x);
-        z.y = (T)0.5 * (xj.y + xm.y) - s * (xj.y - xm.y);
-        return z;
+        const C dif = csub(xj, xm);
+        if (j == 0) anchor = cfma(dif, (T)0.5, anchor);
+        else anchor = cfma(xj, w.x, anchor);
+        return cfma(dif, -s, cscale(cadd(xj, xm), (T)0.5));
     }
 
     // V (natural, unknown index) -> pre-processing -> DFT_N -> Z (natural order).
@@ -273,11 +263,11 @@ struct Eng {
             if (k < H) {
                 const C zk = buf[k * LD + c];
                 const C zm = buf[((N - k) & (N - 1)) * LD + c];
-                C Rk, Ik;
-                Rk.x = (T)0.5 * (zk.x + zm.x);
-                Rk.y = (T)0.5 * (zk.y + zm.y);
-                Ik.x = (T)0.5 * (zm.y - zk.y);
-                Ik.y = (T)0.5 * (zk.x - zm.x);
+                const C Rk = cscale(cadd(zk, zm), (T)0.5);
+                const C d = csub(zk, zm);
+                C Ik;
+                Ik.x = (T)-0.5 * d.y;
+                Ik.y = (T)0.5 * d.x;
                 if (bc == SFRD_BC_PERIODIC) {
                     ev[t] = cadd(Rk, Ik);     // T_k
                     od[t] = csub(Rk, Ik);     // T_{N-k}
