@@ -188,7 +188,8 @@ int sfrd_inverse(sfrd_plan_t plan, const void* uhat, void* u);
  * uhat are caller-owned device fields [S][...] (same layout and result as
  * sfrd_forward); stream is a cudaStream_t (NULL: legacy default stream).
  * The first call on a device looks up that array's device address (once per
- * device, with the device current).  Every call shares the array and leaves its
+ * device, with the device current); make that first call on each device before
+ * any stream capture is in progress.  Every call shares the array and leaves its
  * contents behind; the call clears what must start at zero.  Calls that
  * overlap on the GPU (other streams, other threads) race on the array, and the
  * plan must not be used by another thread during the call.  Synchronises the

@@ -28,7 +28,8 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device, looked up by the first call on each
+// device (with that device current); that first call should come before any stream capture.
 int scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
