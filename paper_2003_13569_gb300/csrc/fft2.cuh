@@ -30,6 +30,8 @@
 // the FFT buffer Z in between; barriers separate the two uses.
 #pragma once
 
+#include <type_traits>
+
 #include "engine.cuh"
 
 namespace sfrd {
@@ -85,27 +87,32 @@ constexpr CS ce_cs2pi(long m, long R) {
     }
 }
 
-// omega_32^m = exp(-2 pi i m / 32), used by the in-register DFTs of length 16 and 32.
-#define SFRD_W32F(m) {(float)ce_cs2pi(m, 32).c, (float)(-ce_cs2pi(m, 32).s)}
-#define SFRD_W32D(m) {ce_cs2pi(m, 32).c, -ce_cs2pi(m, 32).s}
-static __constant__ float2 kW32f[32] = {
-    SFRD_W32F(0),  SFRD_W32F(1),  SFRD_W32F(2),  SFRD_W32F(3),  SFRD_W32F(4),  SFRD_W32F(5),  SFRD_W32F(6),
-    SFRD_W32F(7),  SFRD_W32F(8),  SFRD_W32F(9),  SFRD_W32F(10), SFRD_W32F(11), SFRD_W32F(12), SFRD_W32F(13),
-    SFRD_W32F(14), SFRD_W32F(15), SFRD_W32F(16), SFRD_W32F(17), SFRD_W32F(18), SFRD_W32F(19), SFRD_W32F(20),
-    SFRD_W32F(21), SFRD_W32F(22), SFRD_W32F(23), SFRD_W32F(24), SFRD_W32F(25), SFRD_W32F(26), SFRD_W32F(27),
-    SFRD_W32F(28), SFRD_W32F(29), SFRD_W32F(30), SFRD_W32F(31)};
-static __constant__ double2 kW32d[32] = {
-    SFRD_W32D(0),  SFRD_W32D(1),  SFRD_W32D(2),  SFRD_W32D(3),  SFRD_W32D(4),  SFRD_W32D(5),  SFRD_W32D(6),
-    SFRD_W32D(7),  SFRD_W32D(8),  SFRD_W32D(9),  SFRD_W32D(10), SFRD_W32D(11), SFRD_W32D(12), SFRD_W32D(13),
-    SFRD_W32D(14), SFRD_W32D(15), SFRD_W32D(16), SFRD_W32D(17), SFRD_W32D(18), SFRD_W32D(19), SFRD_W32D(20),
-    SFRD_W32D(21), SFRD_W32D(22), SFRD_W32D(23), SFRD_W32D(24), SFRD_W32D(25), SFRD_W32D(26), SFRD_W32D(27),
-    SFRD_W32D(28), SFRD_W32D(29), SFRD_W32D(30), SFRD_W32D(31)};
-#undef SFRD_W32F
-#undef SFRD_W32D
+// a * omega_32^M, omega_32 = exp(-2 pi i / 32), with M a compile-time constant: the quarter
+// turns are exchanges and sign changes, the rest multiplies by literal constants.
+template <int M, typename C> __device__ __forceinline__ C mul_w32(C a) {
+    using T = decltype(a.x);
+    constexpr int m = ((M % 32) + 32) % 32;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (m == 8) {
+        return mul_mi(a);
+    } else if constexpr (m == 16) {
+        return cneg(a);
+    } else if constexpr (m == 24) {
+        C r; r.x = -a.y; r.y = a.x; return r;
+    } else {
+        constexpr T wr = (T)ce_cs2pi(m, 32).c, wi = (T)(-ce_cs2pi(m, 32).s);
+        C r; r.x = a.x * wr - a.y * wi; r.y = a.x * wi + a.y * wr; return r;
+    }
+}
 
-template <typename C> __device__ __forceinline__ C w32(int m);
-template <> __device__ __forceinline__ float2 w32<float2>(int m) { return kW32f[m]; }
-template <> __device__ __forceinline__ double2 w32<double2>(int m) { return kW32d[m]; }
+// Compile-time loop: f(std::integral_constant<int, i>) for i = B .. E-1.
+template <int B, int E, class F> __device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>());
+        static_for<B + 1, E>(f);
+    }
+}
 
 // ---- in-register DFTs of length 2..32 (natural order in and out) -----------------
 
@@ -118,16 +125,17 @@ template <int R, int Ra, typename C> struct FourStep {
     static constexpr int Rb = R / Ra;
     static __device__ __forceinline__ void run(C* a) {
         C t[R];
-#pragma unroll
-        for (int j2 = 0; j2 < Rb; ++j2) {
+        static_for<0, Rb>([&](auto J2) {
+            constexpr int j2 = decltype(J2)::value;
             C u[Ra];
 #pragma unroll
             for (int j1 = 0; j1 < Ra; ++j1) u[j1] = a[Rb * j1 + j2];
             RDft<Ra, C>::run(u);
-#pragma unroll
-            for (int k1 = 0; k1 < Ra; ++k1)
-                t[j2 * Ra + k1] = (j2 * k1 == 0) ? u[k1] : cmul(u[k1], w32<C>((j2 * k1 * (32 / R)) % 32));
-        }
+            static_for<0, Ra>([&](auto K1) {
+                constexpr int k1 = decltype(K1)::value;
+                t[j2 * Ra + k1] = mul_w32<j2 * k1 * (32 / R)>(u[k1]);
+            });
+        });
 #pragma unroll
         for (int k1 = 0; k1 < Ra; ++k1) {
             C w[Rb];

@@ -248,32 +248,31 @@ __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char
     __syncthreads();
     E::forward(buf, red2, bc, tws, twstride, c, g);
     if (MODE == MODE_REACT) {
-        E::post(buf, red, red2, bc, c, g, [&](int i, C v) { buf[i * LD + c] = v; });
-        __syncthreads();
-        // pointwise reaction on the physical values (kept out of the unrolled code)
-        const double t = a.clock->t0 + ((double)a.clock->k + a.stage_frac) * a.tau;
         const int rA = r0 + c, rB = rA + shiftB;
         T* sv = a.save ? a.save + (long long)rA * a.out_pitch : nullptr;   // stage save (adjoint recomputation)
         if (a.S == 2 && !sv) {
-            // two-species kinds: one loop per kind so that the reaction's switch is resolved at compile time
-            auto loop = [&](auto kind) {
-#pragma unroll 4
-                for (int i = g; i < n; i += G) {
-                    const C v = buf[i * LD + c];
+            // two-species kinds: the pointwise reaction is applied to each physical value as the
+            // transform unpacks it (one unpacking per kind, so that the kind is a compile-time constant)
+            auto run = [&](auto kind) {
+                E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
                     C f;
                     react2k<T>(decltype(kind)::value, a.re, v.x, v.y, f.x, f.y);
                     buf[i * LD + c] = f;
-                }
+                });
             };
             switch (a.re.kind) {
-                case SFRD_REACT_SCHNAKENBERG: loop(std::integral_constant<int, SFRD_REACT_SCHNAKENBERG>()); break;
-                case SFRD_REACT_GRAY_SCOTT: loop(std::integral_constant<int, SFRD_REACT_GRAY_SCOTT>()); break;
-                case SFRD_REACT_FHN: loop(std::integral_constant<int, SFRD_REACT_FHN>()); break;
-                case SFRD_REACT_GIERER_MEINHARDT: loop(std::integral_constant<int, SFRD_REACT_GIERER_MEINHARDT>()); break;
-                case SFRD_REACT_LINEAR: loop(std::integral_constant<int, SFRD_REACT_LINEAR>()); break;
-                default: loop(std::integral_constant<int, SFRD_REACT_NONE>()); break;
+                case SFRD_REACT_SCHNAKENBERG: run(std::integral_constant<int, SFRD_REACT_SCHNAKENBERG>()); break;
+                case SFRD_REACT_GRAY_SCOTT: run(std::integral_constant<int, SFRD_REACT_GRAY_SCOTT>()); break;
+                case SFRD_REACT_FHN: run(std::integral_constant<int, SFRD_REACT_FHN>()); break;
+                case SFRD_REACT_GIERER_MEINHARDT: run(std::integral_constant<int, SFRD_REACT_GIERER_MEINHARDT>()); break;
+                case SFRD_REACT_LINEAR: run(std::integral_constant<int, SFRD_REACT_LINEAR>()); break;
+                default: run(std::integral_constant<int, SFRD_REACT_NONE>()); break;
             }
         } else {
+            E::post(buf, red, red2, bc, c, g, [&](int i, C v) { buf[i * LD + c] = v; });
+            __syncthreads();
+            // pointwise reaction on the physical values, saved for the adjoint recomputation when asked
+            const double t = a.clock->t0 + ((double)a.clock->k + a.stage_frac) * a.tau;
 #pragma unroll 1
             for (int i = g; i < n; i += G) {
                 const C v = buf[i * LD + c];
