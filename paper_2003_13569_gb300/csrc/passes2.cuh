@@ -12,12 +12,13 @@
 namespace sfrd {
 namespace v2 {
 
-// Blocks per SM the register allocation is sized for: 64-80 registers per thread for
-// FP32 lines up to 256, 128 for longer lines and for FP64, 255 for FP64 at 512-1024.
+// Blocks per SM the register allocation is sized for: 64 registers per thread for FP32 lines up
+// to 256 (80 for the update pass, whose batches carry eight values per element), 128 for longer
+// lines and for FP64, 255 for FP64 at 512-1024.
 template <typename T, int N, int MODE>
 constexpr int min_blocks() {
     return sizeof(T) == 8 ? (N >= 512 ? 1 : 2)
-                          : (N >= 512 ? 2 : ((MODE == MODE_PLAIN || MODE == MODE_REACT) ? 4 : 3));
+                          : (N >= 512 ? 2 : (MODE == MODE_TD ? 3 : 4));
 }
 
 template <typename T, int N, int BCT = -1>
@@ -103,7 +104,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         // values read by the combination: batch-loaded (all loads of a batch before any use)
         using V2 = typename Cx<T>::type;                                    // (Q13, phi) pair
         constexpr int NV = MODE == MODE_TD ? 8 : (MODE == MODE_TC ? 4 : (MODE == MODE_T0 ? 1 : 3));
-        constexpr int B = (MODE == MODE_TA || MODE == MODE_TB) ? 2 : 1;
+        constexpr int B = 1;
         T ld[2 * B][2][NV];
         const bool ok[2] = {okA, okB};
         auto pre = [&](int slot, int k) {
