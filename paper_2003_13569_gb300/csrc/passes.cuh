@@ -450,9 +450,15 @@ static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>&
     const int ny = p.n[1];
     a.in = in.ptr;
     a.out = const_cast<T*>(out.ptr);
-    const bool two = p.S == 2;
     const bool use2 = p.v2[d];
     const int cc = use2 ? v2::cc_for(sizeof(T) == 8, (int)p.Nint[d]) : p.CC;
+    // The two real lines of a tile column: the two species at one x, or (one species, and the
+    // middle axis of a 3D grid whose species planes follow one another along blockIdx.y) the
+    // columns x and x + cc, so that a tile row is 2 cc consecutive values of one array row.
+    const bool species_rows = p.S == 2 && d == 1 && p.dim == 3 &&
+                              in.plane == (long long)p.n[2] * ny * in.pitch &&
+                              out.plane == (long long)p.n[2] * ny * out.pitch;
+    const bool two = p.S == 2 && !species_rows;
     a.bshift = two ? 0 : cc;
     a.xw = two ? cc : 2 * cc;
     a.in_offB = two ? in.plane : cc;
@@ -464,12 +470,12 @@ static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>&
         a.out_sAxis = (long long)ny * out.pitch;
         a.out_sOther = out.pitch;
         gy = ny;
-    } else if (p.dim == 3) {   // y in 3D: blockIdx.y = z
+    } else if (p.dim == 3) {   // y in 3D: blockIdx.y = z (+ n_z * species)
         a.in_sAxis = in.pitch;
         a.in_sOther = (long long)ny * in.pitch;
         a.out_sAxis = out.pitch;
         a.out_sOther = (long long)ny * out.pitch;
-        gy = p.n[2];
+        gy = p.n[2] * (species_rows ? p.S : 1);
     } else {               // y in 2D
         a.in_sAxis = in.pitch;
         a.in_sOther = 0;

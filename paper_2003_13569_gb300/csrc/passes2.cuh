@@ -61,7 +61,29 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     const size_t org_out = (size_t)by * (size_t)a.out_sOther + (size_t)xA;
     const unsigned s_in = (unsigned)a.in_sAxis, s_out = (unsigned)a.out_sAxis;
 
-    {
+    if (MODE == MODE_PLAIN && a.bshift == CC && a.in_offB == (long long)CC) {
+        // lines A and B are the columns x and x + CC of one array: a tile row is 2 CC consecutive
+        // values, read by one warp instruction (LW lanes per row) and stored to the .x (A) or .y (B)
+        // halves of the row; all loads of this thread are issued before any shared-memory store
+        constexpr int LW = 2 * CC, RPI = 32 / LW, NW = kThreads / 32;
+        constexpr int NRW = (E::ROWS + NW * RPI - 1) / (NW * RPI);
+        const int w = tid >> 5, l = tid & 31, col = l % LW, sub = l / LW;
+        const int x = bx * a.xw + col;
+        const bool okx = x < a.in_xlim;
+        const T* p = a.in + ((size_t)by * (size_t)a.in_sOther + (size_t)x);
+        T* const dst = reinterpret_cast<T*>(buf) + 2 * (col % CC) + col / CC;
+        T v[NRW];
+#pragma unroll
+        for (int r = 0; r < NRW; ++r) {
+            const int i = (w * RPI + sub) + r * NW * RPI;
+            v[r] = (okx && i < n) ? p[(unsigned)i * s_in] : (T)0;
+        }
+#pragma unroll
+        for (int r = 0; r < NRW; ++r) {
+            const int i = (w * RPI + sub) + r * NW * RPI;
+            if (i < n) dst[2 * i * LD] = v[r];
+        }
+    } else {
         // all loads of this thread issued before any shared-memory store
         constexpr int NL = (E::ROWS + G - 1) / G;
         const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
