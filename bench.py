@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--rational-steps", type=int, default=50,
+                    help="steps timed for the rational-coefficient variant (0: skip)")
     return ap.parse_args()
 
 
@@ -279,6 +281,39 @@ def main():
         extra["fp32_vs_fp64_rel_l2"] = {"value": err, "steps": args.fp64_steps}
         del s64
         torch.cuda.empty_cache()
+
+        # the rational-coefficient variant: L = kappa tau Lambda^(alpha/2) computed in FP64 and stored in
+        # FP32 (one plane shared by the species when their orders agree), the Pade(1,3) coefficients
+        # evaluated in FP32 inside the slow-axis passes; its own pass model (fewer coefficient words)
+        if args.rational_steps > 0:
+            sr = sf.Solver(cfg, dtype="f32", coefficients="rational")
+            sr.load(u0_dev, 0.0)
+            sr.advance(args.warmup)
+            torch.cuda.synchronize()
+            r0 = torch.cuda.Event(enable_timing=True)
+            r1 = torch.cuda.Event(enable_timing=True)
+            r0.record(sr.stream)
+            sr.advance(args.rational_steps)
+            r1.record(sr.stream)
+            torch.cuda.synchronize()
+            msr = r0.elapsed_time(r1)
+            gotr = sr.run(u0_dev, nsteps=args.fp64_steps).double()
+            errr = float(torch.linalg.vector_norm(gotr - ref) / torch.linalg.vector_norm(ref))
+            shared = len(cfg["alpha"]) == 2 and cfg["alpha"][0] == cfg["alpha"][1]
+            lw = 0.5 if shared else 1.0            # words of L per unknown, per slow-axis pass
+            coef_words = {2: 2, 3: 2, 4: 2, 5: 4}  # stored coefficient words per pass kind
+            rwords = sum((WORDS[kd] - coef_words.get(kd, 0) + (lw if kd in coef_words else 0)) * len(ts) / nprof
+                         for kd, ts in prof.items())
+            rbytes = rwords * dof * esize
+            extra["rational_coefficients"] = {
+                "value": dof * args.rational_steps / (msr * 1e-3), "unit": "DOF-steps/s",
+                "ms_per_step": msr / args.rational_steps, "steps": args.rational_steps,
+                "model_words_per_dof_step": rwords,
+                "frac_of_" + peak_kind: rbytes / (msr * 1e-3 / args.rational_steps) / 1e9 / peak,
+                "fp32_vs_fp64_rel_l2": {"value": errr, "steps": args.fp64_steps},
+                "shared_l_plane": shared}
+            del sr
+            torch.cuda.empty_cache()
 
     # the batched workload: 256 Gierer-Meinhardt instances, one persistent launch per pass
     if rank == 0 and args.batched_steps > 0:

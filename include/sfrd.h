@@ -124,6 +124,28 @@ int sfrd_plan(sfrd_plan_t* out, const sfrd_grid* grid, int32_t bc,
               const double* alpha, const double* kappa, double dt,
               int32_t dtype, const sfrd_reaction* reaction);
 
+/* How the slow-axis combination obtains the Padé(1,3) coefficients R13, Q13,
+ * phi, phi1, phi2, phi3 of L = kappa tau Lambda^{alpha/2} (Algorithm 1,
+ * precompute lines; Eq. 37 and the rational forms of its phi-functions):
+ *   SFRD_COEF_STORED   : the six arrays are computed in FP64 at bind time and
+ *                        stored in the run precision (default; 10 words per
+ *                        unknown and step are read by the four combinations);
+ *   SFRD_COEF_RATIONAL : only L is stored (computed in FP64 at bind time and
+ *                        rounded to FP32; one array shared by both species when
+ *                        their orders are equal, as tau Lambda^{alpha/2}); the
+ *                        rationals are evaluated in FP32 inside the passes.
+ *                        They have no cancellation for small L, so the
+ *                        coefficients keep FP32 accuracy; 2 (shared) or 4 words
+ *                        per unknown and step instead of 10.
+ * Call before sfrd_bind (it changes sfrd_workspace_bytes).  SFRD_COEF_RATIONAL
+ * needs an FP32 plan whose axes all have power-of-two N in [64, 1024]; such a
+ * plan has no adjoint (sfrd_adjoint* return SFRD_EUNSUPPORTED) and
+ * sfrd_coefficients evaluates the rationals from the stored L.
+ * Errors: SFRD_EINVAL (mode), SFRD_EUNSUPPORTED, SFRD_ESTATE (already bound). */
+#define SFRD_COEF_STORED   0
+#define SFRD_COEF_RATIONAL 1
+int sfrd_set_coefficients(sfrd_plan_t plan, int32_t mode);
+
 /* Bytes of device workspace the plan needs (coefficient arrays, spectral state
  * and stored stage spectra, scratch, tables). */
 int sfrd_workspace_bytes(sfrd_plan_t plan, size_t* bytes);

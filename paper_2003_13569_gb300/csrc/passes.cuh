@@ -19,6 +19,7 @@
 // the inverse is F / C.  All passes run in place on the work array.
 #pragma once
 
+#include "coef.cuh"
 #include "engine.cuh"
 #include "reaction.cuh"
 
@@ -297,6 +298,52 @@ __global__ void coef_init_kernel(const double* __restrict__ lx, const double* __
     }
 }
 
+// Rational-coefficient mode: L (or tau Lambda^{alpha/2} shared by the species) in FP64, stored in T.
+template <typename T>
+__global__ void coef_l_kernel(const double* __restrict__ lx, const double* __restrict__ ly,
+                              const double* __restrict__ lz, int nx, int ny, int nz, int pitch, int planes,
+                              bool shared, double a0, double a1, double k0, double k1, double tau,
+                              T* __restrict__ CL) {
+    const long long total = (long long)planes * nz * ny * pitch;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % pitch);
+        long long r = idx / pitch;
+        const int y = (int)(r % ny);
+        r /= ny;
+        const int z = (int)(r % nz);
+        const int s = (int)(r / nz);
+        double v = 0;
+        if (x < nx) {
+            const double Lam = lx[x] + ly[y] + lz[z];
+            const double alpha = s == 0 ? a0 : a1, kappa = shared ? 1.0 : (s == 0 ? k0 : k1);
+            v = kappa * tau * (Lam > 0.0 ? pow(Lam, 0.5 * alpha) : 0.0);
+        }
+        CL[idx] = (T)v;
+    }
+}
+
+// Coefficient `which` evaluated from the stored L (rational mode), in T, to dense [S][nz][ny][nx].
+template <typename T>
+__global__ void coef_eval_kernel(const T* __restrict__ CL, bool shared, double k0, double k1, double tau, int which,
+                                 int nx, int ny, int nz, int pitch, int S, T* __restrict__ out) {
+    const long long total = (long long)S * nz * ny * nx;
+    const long long plane = (long long)nz * ny * pitch;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % nx);
+        const long long row = idx / nx;                 // s * nz * ny + (z * ny + y)
+        const int s = (int)(row / ((long long)nz * ny));
+        const long long j = (row - (long long)s * nz * ny) * pitch + x;
+        const T L = shared ? (T)(s == 0 ? k0 : k1) * CL[j] : CL[s * plane + j];
+        T Q, ph, R, p1, p2, p3;
+        p13_qphi<T>(L, (T)tau, Q, ph);
+        p13_rphi<T>(L, (T)tau, R, p1, p2, p3);
+        const T v[6] = {R, Q, ph, p1, p2, p3};
+        out[idx] = v[which];
+    }
+}
+
 // which: 0 R13, 1 Q13, 2 phi, 3 phi1, 4 phi2, 5 phi3 -> dense [S][nz][ny][nx]
 template <typename T>
 __global__ void coef_copy_kernel(const T* __restrict__ CQ, const T* __restrict__ CR, int which, int nx,
@@ -495,6 +542,13 @@ static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>&
     a.F3 = wsT<T>(p, p.off_F3);
     a.CQ = wsT<T>(p, p.off_CQ);
     a.CR = wsT<T>(p, p.off_CR);
+    a.CL = nullptr;
+    if (p.coef_mode == SFRD_COEF_RATIONAL) {
+        a.CQ = a.CR = nullptr;
+        a.CL = wsT<T>(p, p.off_CL);
+        for (int h = 0; h < 2; ++h) a.cl_mult[h] = p.cl_shared ? p.kappa[h] : 1.0;
+        a.clB = p.cl_shared ? 0 : a.in_offB;
+    }
     a.clock = reinterpret_cast<Clock*>(p.ws + p.off_clock);
     a.ax = axis_dev<T>(p, d);
     a.dim = p.dim;
@@ -708,13 +762,24 @@ cudaError_t launch_coef_init(Plan& p, cudaStream_t s) {
     const double* lz = reinterpret_cast<const double*>(p.ws + p.off_lam[2]);
     const double a1 = p.S == 2 ? p.alpha[1] : p.alpha[0];
     const double k1 = p.S == 2 ? p.kappa[1] : p.kappa[0];
-    coef_init_kernel<T><<<1024, 256, 0, s>>>(lx, ly, lz, p.n[0], p.n[1], p.n[2], p.pitch, p.S, p.alpha[0], a1,
-                                             p.kappa[0], k1, p.dt, wsT<T>(p, p.off_CQ), wsT<T>(p, p.off_CR));
+    if (p.coef_mode == SFRD_COEF_RATIONAL)
+        coef_l_kernel<T><<<1024, 256, 0, s>>>(lx, ly, lz, p.n[0], p.n[1], p.n[2], p.pitch, p.cl_shared ? 1 : p.S,
+                                              p.cl_shared, p.alpha[0], a1, p.kappa[0], k1, p.dt,
+                                              wsT<T>(p, p.off_CL));
+    else
+        coef_init_kernel<T><<<1024, 256, 0, s>>>(lx, ly, lz, p.n[0], p.n[1], p.n[2], p.pitch, p.S, p.alpha[0], a1,
+                                                 p.kappa[0], k1, p.dt, wsT<T>(p, p.off_CQ), wsT<T>(p, p.off_CR));
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_coef_copy(Plan& p, int which, void* out, cudaStream_t s) {
+    if (p.coef_mode == SFRD_COEF_RATIONAL) {
+        const double k1 = p.S == 2 ? p.kappa[1] : p.kappa[0];
+        coef_eval_kernel<T><<<1024, 256, 0, s>>>(wsT<T>(p, p.off_CL), p.cl_shared, p.kappa[0], k1, p.dt, which, p.n[0],
+                                                 p.n[1], p.n[2], p.pitch, p.S, static_cast<T*>(out));
+        return cudaGetLastError();
+    }
     coef_copy_kernel<T><<<1024, 256, 0, s>>>(wsT<T>(p, p.off_CQ), wsT<T>(p, p.off_CR), which, p.n[0], p.n[1], p.n[2],
                                              p.pitch, p.S, static_cast<T*>(out));
     return cudaGetLastError();

@@ -6,6 +6,7 @@
 
 #include <type_traits>
 
+#include "coef.cuh"
 #include "fft2.cuh"
 #include "reaction.cuh"
 
@@ -37,7 +38,8 @@ __device__ __forceinline__ int unknowns(int n_runtime) {
     return BCT == SFRD_BC_PERIODIC ? N : (BCT == SFRD_BC_DIRICHLET ? N - 1 : (BCT == SFRD_BC_NEUMANN ? N + 1 : n_runtime));
 }
 
-template <typename T, int N, int MODE, int BCT = -1>
+// RAT: the combination evaluates the coefficients from L (rational-coefficient mode).
+template <typename T, int N, int MODE, int BCT = -1, bool RAT = false>
 __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, unsigned char* smem_raw) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N, BCT>::E;
@@ -129,6 +131,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         constexpr int B = 1;
         T ld[2 * B][2][NV];
         const bool ok[2] = {okA, okB};
+        const unsigned clB = (unsigned)a.clB;
         auto pre = [&](int slot, int k) {
             const unsigned eA = e0 + (unsigned)k * s_in;
 #pragma unroll
@@ -137,7 +140,20 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                 const unsigned i = eA + (h ? eoB : 0u);
                 // read-only inputs through the non-coherent path (every element is read once,
                 // before its own update); coefficient pairs and quads as single vector loads
-                if (MODE == MODE_TA || MODE == MODE_TB || MODE == MODE_TC) {
+                if (RAT) {
+                    const T Lraw = __ldg(a.CL + eA + (h ? clB : 0u));
+                    if (MODE == MODE_TD) {
+                        ld[slot][h][4] = Lraw;
+                        ld[slot][h][0] = __ldg(a.U + i);
+                        ld[slot][h][1] = __ldg(a.F1 + i);
+                        ld[slot][h][2] = __ldg(a.F2 + i);
+                        ld[slot][h][3] = __ldg(a.F3 + i);
+                    } else if (MODE != MODE_T0) {
+                        ld[slot][h][0] = Lraw;
+                        ld[slot][h][2] = __ldg(a.U + i);
+                        if (MODE == MODE_TC) ld[slot][h][3] = __ldg(a.F1 + i);
+                    }
+                } else if (MODE == MODE_TA || MODE == MODE_TB || MODE == MODE_TC) {
                     const V2 q = __ldg(reinterpret_cast<const V2*>(a.CQ) + i);
                     ld[slot][h][0] = q.x;
                     ld[slot][h][1] = q.y;
@@ -167,6 +183,8 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
             }
         };
         T* const F4 = a.F4;
+        const T lm[2] = {(T)a.cl_mult[0], (T)a.cl_mult[1]};
+        const T tau = (T)a.tau;
         E::post_b<B>(buf, red, red2, bc, c, g, pre, [&](int slot, int k, C Fv) {
             const unsigned eA = e0 + (unsigned)k * s_in;
             const T F[2] = {Fv.x, Fv.y};
@@ -175,7 +193,14 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
                 const unsigned i = eA + (h ? eoB : 0u);
-                const T* L = ld[slot][h];
+                T Lc[NV];
+#pragma unroll
+                for (int m = 0; m < NV; ++m) Lc[m] = ld[slot][h][m];
+                if (RAT) {   // coefficients in place of the stored ones: (Q, phi) or (R, phi1, phi2, phi3)
+                    if (MODE == MODE_TD) p13_rphi<T>(lm[h] * Lc[4], tau, Lc[4], Lc[5], Lc[6], Lc[7]);
+                    else if (MODE != MODE_T0) p13_qphi<T>(lm[h] * Lc[0], tau, Lc[0], Lc[1]);
+                }
+                const T* L = Lc;
                 if (MODE == MODE_T0) {
                     a.U[i] = F[h];
                     s[h] = F[h];
@@ -214,10 +239,10 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     if (MODE == MODE_TD && bx == 0 && by == 0 && threadIdx.x == 0) a.clock->k += 1;
 }
 
-template <typename T, int N, int MODE, int BCT = -1>
+template <typename T, int N, int MODE, int BCT = -1, bool RAT = false>
 __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) col2_kernel(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    col2_body<T, N, MODE, BCT>(a, blockIdx.x, blockIdx.y, smem_raw);
+    col2_body<T, N, MODE, BCT, RAT>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 template <typename T, int N, int MODE, int BCT = -1>
@@ -354,6 +379,21 @@ template <typename T, int N, int BCT>
 cudaError_t col2_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
     const size_t smem = TileOf<T, N>::E::smem_bytes();
     void (*k)(const ColArgs<T>) = nullptr;
+    if constexpr (sizeof(T) == 4) {
+        if (a.CL) {   // rational-coefficient mode
+            switch (mode) {
+                case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, true>; break;
+                case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, true>; break;
+                case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, true>; break;
+                case MODE_TD: k = col2_kernel<T, N, MODE_TD, BCT, true>; break;
+                default: break;
+            }
+        }
+    }
+    if (k) {
+        k<<<grid, kThreads, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     switch (mode) {
         case MODE_PLAIN: k = col2_kernel<T, N, MODE_PLAIN, BCT>; break;
         case MODE_T0: k = col2_kernel<T, N, MODE_T0, BCT>; break;
@@ -385,6 +425,15 @@ cudaError_t prepare2_bc() {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
+    }
+    if constexpr (sizeof(T) == 4) {
+        void (*kr[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_TA, BCT, true>, col2_kernel<T, N, MODE_TB, BCT, true>,
+                                          col2_kernel<T, N, MODE_TC, BCT, true>, col2_kernel<T, N, MODE_TD, BCT, true>};
+        for (auto k : kr) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (e != cudaSuccess) return e;
+        }
     }
     void (*xs[])(const XArgs<T>) = {x2_kernel<T, N, MODE_PLAIN, BCT>, x2_kernel<T, N, MODE_REACT, BCT>};
     for (auto k : xs) {

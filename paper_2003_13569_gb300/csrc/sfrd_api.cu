@@ -102,6 +102,36 @@ static int unknowns(int bc, long long N) {
     return bc == SFRD_BC_PERIODIC ? (int)N : (bc == SFRD_BC_DIRICHLET ? (int)N - 1 : (int)N + 1);
 }
 
+// Workspace layout (byte offsets) for the plan's coefficient mode.
+static void layout_workspace(Plan* p) {
+    const int S = p->S;
+    const size_t E = p->esize, fld = (size_t)S * p->plane * E;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+    p->off_W = take(fld);
+    p->off_W2 = take(fld);
+    p->off_U = take(fld);
+    p->off_F1 = take(fld);
+    p->off_F2 = take(fld);
+    p->off_F3 = take(fld);
+    if (p->coef_mode == SFRD_COEF_RATIONAL) {
+        p->off_CQ = p->off_CR = 0;
+        p->off_CL = take((size_t)(p->cl_shared ? 1 : S) * p->plane * E);
+    } else {
+        p->off_CQ = take(2 * fld);
+        p->off_CR = take(4 * fld);
+        p->off_CL = 0;
+    }
+    p->off_D = take((size_t)S * p->dense * E);
+    p->off_clock = take(sizeof(Clock));
+    for (int d = 0; d < 3; ++d) {
+        p->off_tw[d] = take((size_t)p->M[d] * 2 * E);
+        p->off_perm[d] = take((size_t)p->M[d] * sizeof(int));
+        p->off_lam[d] = take(p->lam[d].size() * sizeof(double));
+    }
+    p->ws_bytes = o;
+}
+
 int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, const double* kappa, double dt,
                   int dtype, const sfrd_reaction* re) {
     if (!out || !g || !alpha || !kappa || !re) return SFRD_EINVAL;
@@ -253,26 +283,7 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
         }
     }
 
-    // workspace layout
-    const size_t E = p->esize, fld = (size_t)S * p->plane * E;
-    size_t o = 0;
-    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
-    p->off_W = take(fld);
-    p->off_W2 = take(fld);
-    p->off_U = take(fld);
-    p->off_F1 = take(fld);
-    p->off_F2 = take(fld);
-    p->off_F3 = take(fld);
-    p->off_CQ = take(2 * fld);
-    p->off_CR = take(4 * fld);
-    p->off_D = take((size_t)S * p->dense * E);
-    p->off_clock = take(sizeof(Clock));
-    for (int d = 0; d < 3; ++d) {
-        p->off_tw[d] = take((size_t)p->M[d] * 2 * E);
-        p->off_perm[d] = take((size_t)p->M[d] * sizeof(int));
-        p->off_lam[d] = take(p->lam[d].size() * sizeof(double));
-    }
-    p->ws_bytes = o;
+    layout_workspace(p);
     *out = p;
     return SFRD_OK;
 }
@@ -296,6 +307,7 @@ AdjLayout adj_layout(const Plan& p, int64_t nsteps, int64_t K) {
 }
 
 static bool adjoint_capable(const Plan& p) {
+    if (p.coef_mode == SFRD_COEF_RATIONAL) return false;   // the adjoint differentiates the stored arrays
     for (int d = 0; d < p.dim; ++d)
         if (!p.v2[d]) return false;
     return true;
@@ -434,6 +446,22 @@ int sfrd_plan(sfrd_plan_t* out, const sfrd_grid* grid, int32_t bc, const double*
     h->p = *p;
     delete p;
     *out = h;
+    return SFRD_OK;
+}
+
+int sfrd_set_coefficients(sfrd_plan_t plan, int32_t mode) {
+    if (!plan) return SFRD_EINVAL;
+    if (mode != SFRD_COEF_STORED && mode != SFRD_COEF_RATIONAL) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (p.ws) return SFRD_ESTATE;
+    if (mode == SFRD_COEF_RATIONAL) {
+        if (p.dtype != SFRD_F32) return SFRD_EUNSUPPORTED;
+        for (int d = 0; d < p.dim; ++d)
+            if (!p.v2[d]) return SFRD_EUNSUPPORTED;
+    }
+    p.coef_mode = mode;
+    p.cl_shared = mode == SFRD_COEF_RATIONAL && p.S == 2 && p.alpha[0] == p.alpha[1];
+    sfrd::layout_workspace(&p);
     return SFRD_OK;
 }
 

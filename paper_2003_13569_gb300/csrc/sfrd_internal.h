@@ -96,6 +96,11 @@ struct ColArgs {
     int dim;
     int S;
     double alpha[2], kappa[2], tau;
+    // SFRD_COEF_RATIONAL: the slow-axis combinations evaluate the coefficients from L = cl_mult[h] *
+    // CL[i + (h ? clB : 0)] (line h of the tile); CL == nullptr with stored coefficient arrays
+    const T* CL;
+    double cl_mult[2];
+    long long clB;
 };
 
 template <typename T>
@@ -145,6 +150,9 @@ struct Plan {
     // workspace layout (byte offsets)
     size_t off_W = 0, off_W2 = 0, off_U = 0, off_F1 = 0, off_F2 = 0, off_F3 = 0;
     size_t off_CQ = 0, off_CR = 0, off_clock = 0, off_D = 0;
+    int coef_mode = 0;          // SFRD_COEF_STORED or SFRD_COEF_RATIONAL
+    bool cl_shared = false;     // rational mode: one plane tau Lambda^{alpha/2} for both species
+    size_t off_CL = 0;
     size_t off_tw[3] = {0, 0, 0}, off_perm[3] = {0, 0, 0}, off_lam[3] = {0, 0, 0};
     size_t ws_bytes = 0;
 

@@ -107,3 +107,28 @@ def test_bind_rejects_short_workspace_without_touching_the_gpu(sfrd):
     assert lib.sfrd_bind(h, ctypes.c_void_p(256), 16, None) == -3     # too small: rejected before any CUDA call
     assert lib.sfrd_load(h, ctypes.c_void_p(256), 0.0) == -3          # not bound
     lib.sfrd_destroy(h)
+
+
+def test_coefficient_mode_selection_on_the_host(sfrd):
+    """SFRD_COEF_RATIONAL (L stored, rationals in FP32) is chosen before binding: it shrinks the
+    workspace by the coefficient arrays, needs FP32 and power-of-two axes, and disables the adjoint."""
+    lib = sfrd.lib()
+    h = _plan(sfrd, N=(64, 64, 1), dtype="f32", alpha=(1.5, 1.5))
+    nb0, nb1, nb2 = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.sfrd_workspace_bytes(h, ctypes.byref(nb0)) == 0
+    assert lib.sfrd_set_coefficients(h, 7) == -1
+    assert lib.sfrd_set_coefficients(h, 1) == 0
+    assert lib.sfrd_workspace_bytes(h, ctypes.byref(nb1)) == 0
+    plane = 65 * 68 * 4                                   # Neumann N=64: 65 x 65 unknowns, pitch 68, FP32
+    assert nb0.value - nb1.value >= 11 * plane - 2048     # (Q,phi) and (R,phi1,phi2,phi3) x 2 species -> one L plane
+    assert lib.sfrd_adjoint_workspace_bytes(h, 10, 5, ctypes.byref(nb2)) == -2
+    assert lib.sfrd_set_coefficients(h, 0) == 0
+    assert lib.sfrd_workspace_bytes(h, ctypes.byref(nb2)) == 0 and nb2.value == nb0.value
+    lib.sfrd_destroy(h)
+    h64 = _plan(sfrd, N=(64, 64, 1), dtype="f64")
+    assert lib.sfrd_set_coefficients(h64, 1) == -2
+    lib.sfrd_destroy(h64)
+    hg = _plan(sfrd, N=(96, 64, 1), dtype="f32")          # 96 runs on the shared-memory engine
+    assert lib.sfrd_set_coefficients(hg, 1) == -2
+    lib.sfrd_destroy(hg)
+    assert lib.sfrd_set_coefficients(None, 1) == -1
