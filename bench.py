@@ -319,6 +319,7 @@ def main():
     if rank == 0 and args.batched_steps > 0:
         cfgs = W.gm_instances(256, seed=3)
         bt = sf.Batch(cfgs, dtype="f32")
+        sched = bt.autotune(steps=2)          # blocks per SM and radix order (shared-memory engine sides)
         bt.load([np.stack(W.initial_fields(c)) for c in cfgs])
         bt.advance(3)
         torch.cuda.synchronize()
@@ -333,6 +334,8 @@ def main():
         extra["batched"] = {"value": bt.dof * args.batched_steps / (msb * 1e-3), "unit": "DOF-steps/s",
                             "ms_per_step": msb / args.batched_steps, "steps": args.batched_steps,
                             "instances": bt.count, "dof": bt.dof, "launches_per_step": bt.launches_per_step,
+                            "schedule": {"blocks_per_sm": sched[0], "radix_order_rule": sched[1],
+                                         "chosen_by": "sfrd_batch_autotune (2 timed steps per candidate)"},
                             "workload": "2D fractional Gierer-Meinhardt, 256 instances, sides %s, BC P/D/N and "
                                         "alpha U(1.2,2] per instance, dt=0.05, FP32" % sides}
         del bt

@@ -146,6 +146,19 @@ int sfrd_plan(sfrd_plan_t* out, const sfrd_grid* grid, int32_t bc,
 #define SFRD_COEF_RATIONAL 1
 int sfrd_set_coefficients(sfrd_plan_t plan, int32_t mode);
 
+/* Autotuner of the radix/tile schedule: for the axes on the shared-memory
+ * engine (lengths that are not powers of two), times `steps` steps with every
+ * tile width and radix-stage order (as factored, reversed, ascending,
+ * descending) and keeps the fastest.  With the environment variable
+ * SFRD_AUTOTUNE_CACHE naming a file, a choice recorded there for the same grid,
+ * boundary condition, precision, species count and device name is reused
+ * without timing, and a new choice is appended.  The plan must be bound; it is
+ * bound again with the chosen schedule, so the resident state is lost (call
+ * sfrd_load afterwards).  Plans whose axes all run on the register engine have
+ * nothing to tune.  chosen (may be NULL) receives {tile width, order rule}.
+ * Errors: SFRD_EINVAL, SFRD_ENOWS, SFRD_ECUDA. */
+int sfrd_autotune(sfrd_plan_t plan, int32_t steps, int32_t* chosen);
+
 /* Bytes of device workspace the plan needs (coefficient arrays, spectral state
  * and stored stage spectra, scratch, tables). */
 int sfrd_workspace_bytes(sfrd_plan_t plan, size_t* bytes);
@@ -282,6 +295,13 @@ int sfrd_batch_load(sfrd_batch_t batch, const void* const* u0, double t0);
 int sfrd_batch_advance(sfrd_batch_t batch, int64_t nsteps);
 int sfrd_batch_store(sfrd_batch_t batch, void* const* u);
 int sfrd_batch_info(sfrd_batch_t batch, int64_t* count, int64_t* dof, int64_t* launches_per_step);
+/* Autotuner of the batched schedule: times `steps` batched steps for each
+ * number of resident blocks per SM (1..4) of the persistent launches and each
+ * radix-stage order of the instances on the shared-memory engine, and keeps the
+ * fastest.  The batch must be bound; it is bound again, so the instances must
+ * be loaded afterwards.  chosen (may be NULL) receives {blocks per SM, order
+ * rule}.  Errors: SFRD_EINVAL, SFRD_ENOWS, SFRD_ECUDA. */
+int sfrd_batch_autotune(sfrd_batch_t batch, int32_t steps, int32_t* chosen);
 void sfrd_batch_destroy(sfrd_batch_t batch);
 
 /* Release the plan and its CUDA graph (not the workspace). */

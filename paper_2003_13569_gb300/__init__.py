@@ -30,7 +30,7 @@ REACTION = {"none": 0, "linear": 1, "fhn": 2, "gray_scott": 3, "schnakenberg": 4
             "gierer_meinhardt": 5, "huxley_mms": 6}
 COEFFICIENTS = ("R13", "Q13", "phi", "phi1", "phi2", "phi3")
 COEF_MODE = {"stored": 0, "rational": 1}
-EXPORTS = ("sfrd_plan", "sfrd_set_coefficients", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
+EXPORTS = ("sfrd_plan", "sfrd_set_coefficients", "sfrd_autotune", "sfrd_batch_autotune", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
            "sfrd_store", "sfrd_run", "sfrd_step", "sfrd_run_host", "sfrd_forward", "sfrd_forward_noalloc", "sfrd_inverse",
            "sfrd_coefficients", "sfrd_profile_step", "sfrd_adjoint_workspace_bytes", "sfrd_run_checkpointed",
            "sfrd_adjoint", "sfrd_batch_plan", "sfrd_batch_workspace_bytes", "sfrd_batch_bind", "sfrd_batch_load",
@@ -60,6 +60,8 @@ _D = ctypes.c_double
 _lib.sfrd_plan.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(Grid), ctypes.c_int32, ctypes.POINTER(_D),
                            ctypes.POINTER(_D), _D, ctypes.c_int32, ctypes.POINTER(Reaction)]
 _lib.sfrd_set_coefficients.argtypes = [_P, ctypes.c_int32]
+_lib.sfrd_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+_lib.sfrd_batch_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
 _lib.sfrd_workspace_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
 _lib.sfrd_get_info.argtypes = [_P, ctypes.POINTER(Info)]
 _lib.sfrd_bind.argtypes = [_P, _P, ctypes.c_size_t, _P]
@@ -253,6 +255,13 @@ class Solver:
         _check(_lib.sfrd_inverse(self.handle, _ptr(uhat), _ptr(out)), "sfrd_inverse")
         return out
 
+    def autotune(self, steps=3):
+        """Pick the fastest radix/tile schedule of the shared-memory engine's axes (the resident state
+        is lost: load afterwards).  Returns (tile width, radix-order rule)."""
+        ch = (ctypes.c_int32 * 2)()
+        _check(_lib.sfrd_autotune(self.handle, int(steps), ch), "sfrd_autotune")
+        return int(ch[0]), int(ch[1])
+
     def coefficients(self, which):
         w = COEFFICIENTS.index(which) if isinstance(which, str) else int(which)
         out = self.empty()
@@ -373,6 +382,13 @@ class Batch:
         for i, f in enumerate(fields):
             arr[i] = f.data_ptr()
         return arr
+
+    def autotune(self, steps=2):
+        """Pick the fastest blocks-per-SM of the persistent launches and radix order of the instances
+        on the shared-memory engine (instances must be loaded afterwards).  Returns (blocks per SM, rule)."""
+        ch = (ctypes.c_int32 * 2)()
+        _check(_lib.sfrd_batch_autotune(self.handle, int(steps), ch), "sfrd_batch_autotune")
+        return int(ch[0]), int(ch[1])
 
     def load(self, fields, t0=0.0):
         t = self.torch

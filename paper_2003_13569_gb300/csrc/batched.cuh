@@ -146,6 +146,7 @@ struct BatchPlan {
     cudaGraphExec_t exec = nullptr;
     bool loaded = false;
     int max_blocks = 0;
+    int blocks_per_sm = 0;   // resident blocks per SM of the persistent launches (0: default 2)
 };
 
 template <typename T>
@@ -206,6 +207,9 @@ static void batch_tables(BatchPlan& b, std::vector<char>& host) {
         b.pmid.off_items = put(mi.data(), mi.size() * sizeof(BatchItem));
         b.pmid.nitems = (int)mi.size();
         b.pmid.smem = sm;
+    } else {
+        b.pmid.off_args = b.pmid.off_items = 0;
+        b.pmid.nitems = 0;
     }
 }
 

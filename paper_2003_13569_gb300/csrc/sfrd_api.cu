@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <cstdio>
 #include "sfrd_internal.h"
 
 namespace sfrd {
@@ -288,6 +290,83 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
     return SFRD_OK;
 }
 
+// ---- schedule of the shared-memory engine and its autotuner ----------------------------
+
+bool has_generic_axis(const Plan& p) {
+    for (int d = 0; d < p.dim; ++d)
+        if (!p.v2[d]) return true;
+    return false;
+}
+
+bool apply_schedule(Plan* p, int cc, int rule) {
+    p->CC = cc;
+    bool fresh = false;
+    for (int d = 0; d < p->dim; ++d) {
+        if (p->v2[d]) continue;
+        std::vector<int> r;
+        factor(p->M[d], r);
+        std::vector<int> base = r;
+        if (rule == 1) std::reverse(r.begin(), r.end());
+        if (rule == 2) std::stable_sort(r.begin(), r.end());
+        if (rule == 3) std::stable_sort(r.begin(), r.end(), [](int x, int y) { return x > y; });
+        // a rule is new for this axis unless an earlier rule (0 .. rule-1) gives the same order
+        bool seen = false;
+        for (int q = 0; q < rule && !seen; ++q) {
+            std::vector<int> o = base;
+            if (q == 1) std::reverse(o.begin(), o.end());
+            if (q == 2) std::stable_sort(o.begin(), o.end());
+            seen = o == r;
+        }
+        fresh = fresh || !seen;
+        p->radix[d] = r;
+        dif_perm(p->M[d], p->radix[d], p->perm[d]);
+    }
+    p->sched_rule = rule;
+    return rule == 0 || fresh;
+}
+
+// Autotuner cache: a text file (path in SFRD_AUTOTUNE_CACHE) of lines "<key> <cc> <rule>"; the last
+// line with a key wins.
+static std::string schedule_key(const Plan& p) {
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) prop.name[0] = 0;
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (ch == ' ') ch = '_';
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "plan:d%d:N%lldx%lldx%lld:bc%d:dt%d:S%d:%s", p.dim, (long long)p.Nint[0],
+                  (long long)p.Nint[1], (long long)p.Nint[2], p.bc, p.dtype, p.S, name.c_str());
+    return buf;
+}
+
+static bool cache_lookup(const std::string& key, int* cc, int* rule) {
+    const char* path = std::getenv("SFRD_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    std::FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char k[256];
+    int a = 0, b = 0;
+    bool hit = false;
+    while (std::fscanf(f, "%255s %d %d", k, &a, &b) == 3)
+        if (key == k) {
+            *cc = a;
+            *rule = b;
+            hit = true;
+        }
+    std::fclose(f);
+    return hit;
+}
+
+static void cache_store(const std::string& key, int cc, int rule) {
+    const char* path = std::getenv("SFRD_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    std::FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d\n", key.c_str(), cc, rule);
+    std::fclose(f);
+}
+
 AdjLayout adj_layout(const Plan& p, int64_t nsteps, int64_t K) {
     AdjLayout L;
     L.nsteps = nsteps;
@@ -462,6 +541,60 @@ int sfrd_set_coefficients(sfrd_plan_t plan, int32_t mode) {
     p.coef_mode = mode;
     p.cl_shared = mode == SFRD_COEF_RATIONAL && p.S == 2 && p.alpha[0] == p.alpha[1];
     sfrd::layout_workspace(&p);
+    return SFRD_OK;
+}
+
+int sfrd_autotune(sfrd_plan_t plan, int32_t steps, int32_t* chosen) {
+    if (!plan || steps < 1) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (!p.ws) return SFRD_ENOWS;
+    int best_cc = p.CC, best_rule = p.sched_rule;
+    if (sfrd::has_generic_axis(p)) {
+        const std::string key = sfrd::schedule_key(p);
+        if (!sfrd::cache_lookup(key, &best_cc, &best_rule)) {
+            const int c32[3] = {16, 8, 4}, c64[3] = {8, 4, 2};
+            const int* cands = p.dtype == SFRD_F32 ? c32 : c64;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            SFRD_CUDA_C(cudaEventCreate(&e0));
+            SFRD_CUDA_C(cudaEventCreate(&e1));
+            float best = -1.0f;
+            int rc = SFRD_OK;
+            for (int i = 0; i < 3 && rc == SFRD_OK; ++i) {
+                for (int rule = 0; rule < 4 && rc == SFRD_OK; ++rule) {
+                    if (!sfrd::apply_schedule(&p, cands[i], rule)) continue;
+                    rc = sfrd::bind_plan(&p, p.ws, p.ws_bytes, p.stream);
+                    if (rc != SFRD_OK) break;
+                    cudaError_t e = sfrd::step_direct(&p, p.stream);   // warm-up
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, p.stream);
+                    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = sfrd::step_direct(&p, p.stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, p.stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e != cudaSuccess) {
+                        rc = sfrd::cuda_fail(e, "sfrd_autotune");
+                        break;
+                    }
+                    if (best < 0 || ms < best) {
+                        best = ms;
+                        best_cc = cands[i];
+                        best_rule = rule;
+                    }
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc != SFRD_OK) return rc;
+            sfrd::cache_store(key, best_cc, best_rule);
+        }
+        sfrd::apply_schedule(&p, best_cc, best_rule);
+        const int rc = sfrd::bind_plan(&p, p.ws, p.ws_bytes, p.stream);   // uploads the chosen tables
+        if (rc != SFRD_OK) return rc;
+    }
+    if (chosen) {
+        chosen[0] = best_cc;
+        chosen[1] = best_rule;
+    }
     return SFRD_OK;
 }
 

@@ -128,7 +128,7 @@ int sfrd_batch_bind(sfrd_batch_t batch, void* workspace, size_t bytes, void* str
     int dev = 0, sms = 0;
     SFRD_BCUDA(cudaGetDevice(&dev));
     SFRD_BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    b.max_blocks = 2 * sms;
+    b.max_blocks = (b.blocks_per_sm > 0 ? b.blocks_per_sm : 2) * sms;
     if (!b.cap_stream) SFRD_BCUDA(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
     SFRD_BCUDA(cudaStreamSynchronize(b.stream));
     return SFRD_OK;
@@ -195,6 +195,57 @@ int sfrd_batch_info(sfrd_batch_t batch, int64_t* count, int64_t* dof, int64_t* l
     if (count) *count = (int64_t)b.inst.size();
     if (dof) *dof = d;
     if (launches_per_step) *launches_per_step = b.dim == 3 ? 16 : 8;
+    return SFRD_OK;
+}
+
+int sfrd_batch_autotune(sfrd_batch_t batch, int32_t steps, int32_t* chosen) {
+    if (!batch || steps < 1) return SFRD_EINVAL;
+    BatchPlan& b = batch->b;
+    if (!b.ws) return SFRD_ENOWS;
+    bool generic = false;
+    for (const Plan& p : b.inst) generic = generic || sfrd::has_generic_axis(p);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SFRD_BCUDA(cudaEventCreate(&e0));
+    SFRD_BCUDA(cudaEventCreate(&e1));
+    float best = -1.0f;
+    int best_k = 2, best_rule = 0, rc = SFRD_OK;
+    for (int rule = 0; rule < (generic ? 4 : 1) && rc == SFRD_OK; ++rule) {
+        bool fresh = rule == 0;
+        for (Plan& p : b.inst) fresh = sfrd::apply_schedule(&p, p.CC, rule) || fresh;
+        if (!fresh) continue;
+        for (int k = 1; k <= 4 && rc == SFRD_OK; ++k) {
+            b.blocks_per_sm = k;
+            rc = sfrd_batch_bind(batch, b.ws, b.ws_bytes, b.stream);
+            if (rc != SFRD_OK) break;
+            cudaError_t e = step_direct(b, b.stream);   // warm-up (state is zero after binding)
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b.stream);
+            for (int q = 0; q < steps && e == cudaSuccess; ++q) e = step_direct(b, b.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b.stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rc = sfrd::cuda_fail(e, "sfrd_batch_autotune");
+                break;
+            }
+            if (best < 0 || ms < best) {
+                best = ms;
+                best_k = k;
+                best_rule = rule;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SFRD_OK) return rc;
+    for (Plan& p : b.inst) sfrd::apply_schedule(&p, p.CC, best_rule);
+    b.blocks_per_sm = best_k;
+    rc = sfrd_batch_bind(batch, b.ws, b.ws_bytes, b.stream);
+    if (rc != SFRD_OK) return rc;
+    if (chosen) {
+        chosen[0] = best_k;
+        chosen[1] = best_rule;
+    }
     return SFRD_OK;
 }
 

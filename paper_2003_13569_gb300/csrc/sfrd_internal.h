@@ -152,6 +152,7 @@ struct Plan {
     size_t off_CQ = 0, off_CR = 0, off_clock = 0, off_D = 0;
     int coef_mode = 0;          // SFRD_COEF_STORED or SFRD_COEF_RATIONAL
     bool cl_shared = false;     // rational mode: one plane tau Lambda^{alpha/2} for both species
+    int sched_rule = 0;         // radix-order rule of the shared-memory engine (apply_schedule)
     size_t off_CL = 0;
     size_t off_tw[3] = {0, 0, 0}, off_perm[3] = {0, 0, 0}, off_lam[3] = {0, 0, 0};
     size_t ws_bytes = 0;
@@ -209,6 +210,11 @@ template <typename T> cudaError_t launch_adjoint(Plan& p, double t0, int64_t nst
 cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s, long long k0 = 0);
 
 int kernels_per_step(const Plan& p);
+// Schedule of the shared-memory engine's axes: tile width cc and the order of the radix stages
+// (rule 0 as factored, 1 reversed, 2 ascending, 3 descending); rebuilds the host permutation tables
+// (uploaded by the next bind).  Returns false when the rule gives the same order as an earlier rule.
+bool apply_schedule(Plan* p, int cc, int rule);
+bool has_generic_axis(const Plan& p);
 
 // Plan construction and binding shared by the single-instance and batched C ABI.
 int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, const double* kappa, double dt,
