@@ -146,6 +146,20 @@ int sfrd_plan(sfrd_plan_t* out, const sfrd_grid* grid, int32_t bc,
 #define SFRD_COEF_RATIONAL 1
 int sfrd_set_coefficients(sfrd_plan_t plan, int32_t mode);
 
+/* Time-stepping scheme (Section 4).  SFRD_SCHEME_P13 (default) is the paper's
+ * ETDRK4-P13: Algorithm 1 with the Padé(1,3) coefficients.  SFRD_SCHEME_COX_MATTHEWS
+ * runs the same stages with the exact-exponential coefficients it approximates
+ * (e^{-L} in the place of R13(L), and the phi-functions of e^{-L}, computed in
+ * FP64 at bind time: Taylor series of the phi-functions for L < 1, closed forms
+ * otherwise); a single eigenmode then decays by exactly exp(-kappa
+ * Lambda^{alpha/2} t) under zero reaction.  Call before sfrd_bind.  The
+ * Cox-Matthews scheme uses stored coefficient arrays (not SFRD_COEF_RATIONAL)
+ * and has no adjoint (sfrd_adjoint* return SFRD_EUNSUPPORTED).
+ * Errors: SFRD_EINVAL (scheme), SFRD_EUNSUPPORTED, SFRD_ESTATE (already bound). */
+#define SFRD_SCHEME_P13           0
+#define SFRD_SCHEME_COX_MATTHEWS  1
+int sfrd_set_scheme(sfrd_plan_t plan, int32_t scheme);
+
 /* Autotuner of the radix/tile schedule: for the axes on the shared-memory
  * engine (lengths that are not powers of two), times `steps` steps with every
  * tile width and radix-stage order (as factored, reversed, ascending,

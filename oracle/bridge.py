@@ -40,4 +40,4 @@ def problem(cfg):
 
 
 def solver(cfg):
-    return O.ETDRK4P13(problem(cfg))
+    return O.ETDRK4P13(problem(cfg), scheme=cfg.get("scheme", "p13"))

@@ -24,6 +24,9 @@ What it computes, in the paper's order and notation:
     (Example 1, Example 2).
   * The discrete adjoint of that step (reverse-mode derivative of the same
     arithmetic), for gradient checks.
+  * The Cox-Matthews variant of the step: the same stages with exact
+    exponentials (e^{-L} in the place of R13(L)), its coefficients evaluated by
+    the Cauchy contour integral.
 
 Readings where the paper is garbled or silent (each pinned by a CPU test):
   R1  periodic eigenvalue angle: sin^2(pi k / N), k = 0..N-1 in DFT order (the
@@ -244,6 +247,59 @@ def p13_coefficients(L, tau: float) -> dict:
     }
 
 
+def cox_matthews_coefficients(L, tau: float, npts: int = 64) -> dict:
+    """The Cox-Matthews ETDRK4 coefficients (exact exponentials) in the places of Algorithm 1's six
+    arrays, for the linear part u_t = -(L/tau) u, z = -L:
+      R13 -> e^{z},  Q13 -> e^{z/2},  phi -> (tau/2) (e^{z/2} - 1)/(z/2),
+      phi1 -> tau [-4 - z + e^{z}(4 - 3z + z^2)] / z^3,
+      phi2 -> 2 tau [2 + z + e^{z}(z - 2)] / z^3,
+      phi3 -> tau [-4 - 3z - z^2 + e^{z}(4 - z)] / z^3,
+    i.e. Algorithm 1 with R13(L) replaced by e^{-L}.  These forms cancel as z -> 0.  For |z| < 2
+    each function is evaluated as its mean over a circle centred at its argument (the trapezoidal
+    rule of the Cauchy integral, npts points, as Kassam and Trefethen do for the ETDRK4
+    coefficients), with radius |z| + 1 so that the circle never comes closer than 1 to the origin,
+    where the forms cancel; for |z| >= 2 the forms are evaluated directly (they lose at most a factor
+    of about 30 there).  This is the exponential-integrator scheme the P13 scheme approximates."""
+    L = np.asarray(L, dtype=np.float64)
+    z = -L
+    unit = np.exp(2j * np.pi * (np.arange(npts) + 0.5) / npts)
+
+    def phi_forms(Z):
+        eZ = np.exp(Z)
+        Z3 = Z ** 3
+        return ((-4.0 - Z + eZ * (4.0 - 3.0 * Z + Z ** 2)) / Z3,
+                (2.0 + Z + eZ * (Z - 2.0)) / Z3,
+                (-4.0 - 3.0 * Z - Z ** 2 + eZ * (4.0 - Z)) / Z3)
+
+    def psi1(Z):
+        return (np.exp(Z) - 1.0) / Z
+
+    def contour(f, w):
+        pts = w[..., None] + (np.abs(w)[..., None] + 1.0) * unit
+        return f(pts).mean(axis=-1).real
+
+    near = np.abs(z) < 2.0
+    zs = np.where(near, 3.0, z)          # any value with |zs| >= 2 where the direct forms are not used
+    d1, d2, d3 = phi_forms(zs)
+    w = z / 2
+    ws = np.where(np.abs(w) < 2.0, 3.0, w)
+    phi_w = np.where(np.abs(w) < 2.0, contour(psi1, w), psi1(ws))
+    c1 = np.where(near, contour(lambda Z: phi_forms(Z)[0], z), d1)
+    c2 = np.where(near, contour(lambda Z: phi_forms(Z)[1], z), d2)
+    c3 = np.where(near, contour(lambda Z: phi_forms(Z)[2], z), d3)
+    return {
+        "R13": np.exp(z),
+        "Q13": np.exp(w),
+        "phi": tau / 2 * phi_w,
+        "phi1": tau * c1,
+        "phi2": 2.0 * tau * c2,
+        "phi3": tau * c3,
+    }
+
+
+SCHEMES = {"p13": p13_coefficients, "cox_matthews": cox_matthews_coefficients}
+
+
 Reaction = Callable[[list, float], list]
 
 
@@ -262,14 +318,17 @@ class Problem:
 
 
 class ETDRK4P13:
-    """Algorithm 1 of the paper for any dimension, boundary condition and species count."""
+    """Algorithm 1 of the paper for any dimension, boundary condition and species count.
+    scheme "cox_matthews" runs the same stages with the exact-exponential coefficients
+    (cox_matthews_coefficients) instead of the Pade-(1,3) ones."""
 
-    def __init__(self, prob: Problem):
+    def __init__(self, prob: Problem, scheme: str = "p13"):
         self.prob = prob
+        self.scheme = scheme
         self.sp = Spectral(prob.grid, prob.bc)
         self.L = [prob.kappa[s] * prob.tau * self.sp.Lambda_frac(prob.alpha[s])
                   for s in range(prob.nspecies)]
-        self.coef = [p13_coefficients(L, prob.tau) for L in self.L]
+        self.coef = [SCHEMES[scheme](L, prob.tau) for L in self.L]
 
     def _real(self, V):
         return V.real if self.prob.bc == PERIODIC else V
@@ -458,6 +517,8 @@ def adjoint_run(solver: ETDRK4P13, u0: list, t0: float, nsteps: int, dldu_T: lis
     dl/dkappa_s = sum dl/dC * dC/dL * tau Lambda^{alpha_s/2};
     dl/dalpha_s = sum dl/dC * dC/dL * kappa_s tau Lambda^{alpha_s/2} ln(Lambda)/2 (0 where Lambda = 0).
     """
+    if solver.scheme != "p13":
+        raise NotImplementedError("the adjoint differentiates the Pade-(1,3) coefficients")
     prob = solver.prob
     S = prob.nspecies
     states = [[np.array(x, dtype=np.float64) for x in u0]]

@@ -30,7 +30,8 @@ REACTION = {"none": 0, "linear": 1, "fhn": 2, "gray_scott": 3, "schnakenberg": 4
             "gierer_meinhardt": 5, "huxley_mms": 6}
 COEFFICIENTS = ("R13", "Q13", "phi", "phi1", "phi2", "phi3")
 COEF_MODE = {"stored": 0, "rational": 1}
-EXPORTS = ("sfrd_plan", "sfrd_set_coefficients", "sfrd_autotune", "sfrd_batch_autotune", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
+SCHEME = {"p13": 0, "cox_matthews": 1}
+EXPORTS = ("sfrd_plan", "sfrd_set_coefficients", "sfrd_set_scheme", "sfrd_autotune", "sfrd_batch_autotune", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
            "sfrd_store", "sfrd_run", "sfrd_step", "sfrd_run_host", "sfrd_forward", "sfrd_forward_noalloc", "sfrd_inverse",
            "sfrd_coefficients", "sfrd_profile_step", "sfrd_adjoint_workspace_bytes", "sfrd_run_checkpointed",
            "sfrd_adjoint", "sfrd_batch_plan", "sfrd_batch_workspace_bytes", "sfrd_batch_bind", "sfrd_batch_load",
@@ -60,6 +61,7 @@ _D = ctypes.c_double
 _lib.sfrd_plan.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(Grid), ctypes.c_int32, ctypes.POINTER(_D),
                            ctypes.POINTER(_D), _D, ctypes.c_int32, ctypes.POINTER(Reaction)]
 _lib.sfrd_set_coefficients.argtypes = [_P, ctypes.c_int32]
+_lib.sfrd_set_scheme.argtypes = [_P, ctypes.c_int32]
 _lib.sfrd_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
 _lib.sfrd_batch_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
 _lib.sfrd_workspace_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
@@ -155,9 +157,12 @@ def make_plan(dim, N, lo, hi, bc, alpha, kappa, dt, dtype, reaction, params=(), 
 class Solver:
     """One plan bound to a torch-allocated workspace on the current CUDA device and stream."""
 
-    def __init__(self, cfg: dict, dtype: str | None = None, device=None, coefficients: str = "stored"):
+    def __init__(self, cfg: dict, dtype: str | None = None, device=None, coefficients: str = "stored",
+                 scheme: str | None = None):
         """coefficients: "stored" (FP64-computed coefficient arrays) or "rational" (L stored, the
-        Padé(1,3) rationals evaluated in FP32 by the passes; FP32 plans on power-of-two grids)."""
+        Padé(1,3) rationals evaluated in FP32 by the passes; FP32 plans on power-of-two grids).
+        scheme: "p13" (the paper's ETDRK4-P13, default) or "cox_matthews" (exact exponentials);
+        defaults to cfg.get("scheme", "p13")."""
         import torch
         self.torch = torch
         self.cfg = cfg
@@ -168,6 +173,9 @@ class Solver:
         self.handle = make_plan(cfg["dim"], cfg["N"], cfg["lo"], cfg["hi"], cfg["bc"], cfg["alpha"],
                                 cfg["kappa"], cfg["dt"], self.dtype, r["kind"], r.get("p", ()),
                                 r.get("offset", (0.0, 0.0)), nspecies=self.S)
+        self.scheme = scheme or cfg.get("scheme", "p13")
+        if self.scheme != "p13":
+            _check(_lib.sfrd_set_scheme(self.handle, SCHEME[self.scheme]), "sfrd_set_scheme")
         if coefficients != "stored":
             _check(_lib.sfrd_set_coefficients(self.handle, COEF_MODE[coefficients]), "sfrd_set_coefficients")
         self.coef_mode = coefficients

@@ -30,4 +30,47 @@ __host__ __device__ __forceinline__ void p13_rphi(T L, T tau, T& R, T& p1, T& p2
     p3 = tau * ((T)4 + L * ((T)3 + L)) * r;
 }
 
+// Cox-Matthews ETDRK4 coefficients (exact exponentials), z = -L <= 0, in the places of the six
+// arrays above: R13 -> e^z, Q13 -> e^{z/2}, phi -> (tau/2) psi1(z/2),
+// phi1 -> tau (psi1 - 3 psi2 + 4 psi3), phi2 -> 2 tau (psi2 - 2 psi3), phi3 -> tau (-psi2 + 4 psi3),
+// with psi_k(z) = sum_{n >= 0} z^n / (n + k)! the phi-functions of exponential integrators.  For
+// |z| < 1 the psi_k are summed from their Taylor series (20 terms: the remainder is below 1e-19);
+// for |z| >= 1 the closed forms e.g. phi1 = tau [-4 - z + e^z (4 - 3z + z^2)] / z^3 are used, whose
+// cancellation is at most a factor ~150 there.  FP64.
+constexpr double cm_inv_fact(int m) {
+    double r = 1.0;
+    for (int i = 2; i <= m; ++i) r /= (double)i;
+    return r;
+}
+#define SFRD_IF4(m) cm_inv_fact(m), cm_inv_fact(m + 1), cm_inv_fact(m + 2), cm_inv_fact(m + 3)
+static __constant__ double kCmInvFact[24] = {SFRD_IF4(0), SFRD_IF4(4), SFRD_IF4(8), SFRD_IF4(12), SFRD_IF4(16),
+                                             SFRD_IF4(20)};
+#undef SFRD_IF4
+
+// sum_{n=0}^{19} z^n / (n+k)!, Horner from the highest term (k <= 3)
+__device__ inline double cm_series(double z, int k) {
+    double acc = kCmInvFact[19 + k];
+    for (int n = 18; n >= 0; --n) acc = acc * z + kCmInvFact[n + k];
+    return acc;
+}
+
+__device__ inline void cm_coefficients(double L, double tau, double& R, double& Q, double& phi,
+                                                double& p1, double& p2, double& p3) {
+    const double z = -L, w = -0.5 * L;
+    R = exp(z);
+    Q = exp(w);
+    phi = 0.5 * tau * (w > -1.0 ? cm_series(w, 1) : (Q - 1.0) / w);
+    if (z > -1.0) {
+        const double s1 = cm_series(z, 1), s2 = cm_series(z, 2), s3 = cm_series(z, 3);
+        p1 = tau * (s1 - 3.0 * s2 + 4.0 * s3);
+        p2 = 2.0 * tau * (s2 - 2.0 * s3);
+        p3 = tau * (-s2 + 4.0 * s3);
+    } else {
+        const double z3 = z * z * z;
+        p1 = tau * (-4.0 - z + R * (4.0 - 3.0 * z + z * z)) / z3;
+        p2 = 2.0 * tau * (2.0 + z + R * (z - 2.0)) / z3;
+        p3 = tau * (-4.0 - 3.0 * z - z * z + R * (4.0 - z)) / z3;
+    }
+}
+
 }  // namespace sfrd

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kThreads) x_kernel(const XArgs<T> a) {
 template <typename T>
 __global__ void coef_init_kernel(const double* __restrict__ lx, const double* __restrict__ ly,
                                  const double* __restrict__ lz, int nx, int ny, int nz, int pitch,
-                                 int S, double a0, double a1, double k0, double k1, double tau,
+                                 int S, double a0, double a1, double k0, double k1, double tau, int scheme,
                                  T* __restrict__ CQ, T* __restrict__ CR) {
     const long long total = (long long)S * nz * ny * pitch;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -280,14 +280,18 @@ __global__ void coef_init_kernel(const double* __restrict__ lx, const double* __
             const double alpha = s == 0 ? a0 : a1, kappa = s == 0 ? k0 : k1;
             const double Lf = Lam > 0.0 ? pow(Lam, 0.5 * alpha) : 0.0;   // Lambda^{alpha/2}
             const double L = kappa * tau * Lf;                  // L = kappa tau Lambda^{alpha/2}
-            const double D1 = 24.0 + L * (18.0 + L * (6.0 + L));
-            const double D2 = 192.0 + L * (72.0 + L * (12.0 + L));
-            R = (24.0 - 6.0 * L) / D1;
-            Q = 24.0 * (8.0 - L) / D2;
-            ph = tau * (96.0 + L * (12.0 + L)) / D2;
-            p1 = tau * (4.0 - L) / D1;
-            p2 = 2.0 * tau * (4.0 + L) / D1;
-            p3 = tau * (4.0 + L * (3.0 + L)) / D1;
+            if (scheme == SFRD_SCHEME_COX_MATTHEWS) {
+                cm_coefficients(L, tau, R, Q, ph, p1, p2, p3);
+            } else {
+                const double D1 = 24.0 + L * (18.0 + L * (6.0 + L));
+                const double D2 = 192.0 + L * (72.0 + L * (12.0 + L));
+                R = (24.0 - 6.0 * L) / D1;
+                Q = 24.0 * (8.0 - L) / D2;
+                ph = tau * (96.0 + L * (12.0 + L)) / D2;
+                p1 = tau * (4.0 - L) / D1;
+                p2 = 2.0 * tau * (4.0 + L) / D1;
+                p3 = tau * (4.0 + L * (3.0 + L)) / D1;
+            }
         }
         CQ[2 * idx] = (T)Q;
         CQ[2 * idx + 1] = (T)ph;
@@ -768,7 +772,8 @@ cudaError_t launch_coef_init(Plan& p, cudaStream_t s) {
                                               wsT<T>(p, p.off_CL));
     else
         coef_init_kernel<T><<<1024, 256, 0, s>>>(lx, ly, lz, p.n[0], p.n[1], p.n[2], p.pitch, p.S, p.alpha[0], a1,
-                                                 p.kappa[0], k1, p.dt, wsT<T>(p, p.off_CQ), wsT<T>(p, p.off_CR));
+                                                 p.kappa[0], k1, p.dt, p.scheme, wsT<T>(p, p.off_CQ),
+                                                 wsT<T>(p, p.off_CR));
     return cudaGetLastError();
 }
 

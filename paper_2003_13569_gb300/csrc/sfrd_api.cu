@@ -387,6 +387,7 @@ AdjLayout adj_layout(const Plan& p, int64_t nsteps, int64_t K) {
 
 static bool adjoint_capable(const Plan& p) {
     if (p.coef_mode == SFRD_COEF_RATIONAL) return false;   // the adjoint differentiates the stored arrays
+    if (p.scheme != SFRD_SCHEME_P13) return false;         // ... of the Padé(1,3) scheme
     for (int d = 0; d < p.dim; ++d)
         if (!p.v2[d]) return false;
     return true;
@@ -534,13 +535,23 @@ int sfrd_set_coefficients(sfrd_plan_t plan, int32_t mode) {
     Plan& p = plan->p;
     if (p.ws) return SFRD_ESTATE;
     if (mode == SFRD_COEF_RATIONAL) {
-        if (p.dtype != SFRD_F32) return SFRD_EUNSUPPORTED;
+        if (p.dtype != SFRD_F32 || p.scheme != SFRD_SCHEME_P13) return SFRD_EUNSUPPORTED;
         for (int d = 0; d < p.dim; ++d)
             if (!p.v2[d]) return SFRD_EUNSUPPORTED;
     }
     p.coef_mode = mode;
     p.cl_shared = mode == SFRD_COEF_RATIONAL && p.S == 2 && p.alpha[0] == p.alpha[1];
     sfrd::layout_workspace(&p);
+    return SFRD_OK;
+}
+
+int sfrd_set_scheme(sfrd_plan_t plan, int32_t scheme) {
+    if (!plan) return SFRD_EINVAL;
+    if (scheme != SFRD_SCHEME_P13 && scheme != SFRD_SCHEME_COX_MATTHEWS) return SFRD_EINVAL;
+    Plan& p = plan->p;
+    if (p.ws) return SFRD_ESTATE;
+    if (scheme == SFRD_SCHEME_COX_MATTHEWS && p.coef_mode != SFRD_COEF_STORED) return SFRD_EUNSUPPORTED;
+    p.scheme = scheme;
     return SFRD_OK;
 }
 

@@ -153,6 +153,7 @@ struct Plan {
     int coef_mode = 0;          // SFRD_COEF_STORED or SFRD_COEF_RATIONAL
     bool cl_shared = false;     // rational mode: one plane tau Lambda^{alpha/2} for both species
     int sched_rule = 0;         // radix-order rule of the shared-memory engine (apply_schedule)
+    int scheme = 0;             // SFRD_SCHEME_P13 or SFRD_SCHEME_COX_MATTHEWS
     size_t off_CL = 0;
     size_t off_tw[3] = {0, 0, 0}, off_perm[3] = {0, 0, 0}, off_lam[3] = {0, 0, 0};
     size_t ws_bytes = 0;

@@ -382,3 +382,80 @@ def test_oracle_adjoint_matches_central_differences(bc):
         um[sp_][i, j] -= hh
         fd = (loss(th, up) - loss(th, um)) / (2 * hh)
         assert gr["u0"][sp_][i, j] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+# --------------------------------------------------------------------------
+# The Cox-Matthews variant (exact exponentials, Section 4's reference scheme)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [1.5, 4.6, 20.0, 300.0])
+def test_cox_matthews_contour_coefficients_match_closed_forms(L):
+    """Away from L = 0 the closed forms do not cancel: the contour means must equal them."""
+    tau = 0.37
+    c = O.cox_matthews_coefficients(np.array([L]), tau)
+    E, E2 = math.exp(-L), math.exp(-L / 2)
+    z = -L
+    assert c["R13"][0] == pytest.approx(E, rel=1e-15)
+    assert c["Q13"][0] == pytest.approx(E2, rel=1e-15)
+    assert c["phi"][0] == pytest.approx(tau * (1 - E2) / L, rel=1e-12)
+    assert c["phi1"][0] == pytest.approx(tau * (-4 - z + E * (4 - 3 * z + z * z)) / z ** 3, rel=1e-11)
+    assert c["phi2"][0] == pytest.approx(2 * tau * (2 + z + E * (z - 2)) / z ** 3, rel=1e-11)
+    assert c["phi3"][0] == pytest.approx(tau * (-4 - 3 * z - z * z + E * (4 - z)) / z ** 3, rel=1e-11)
+
+
+def test_cox_matthews_coefficients_zero_limits_and_small_l_series():
+    """L -> 0: the classical RK4 weights; small L: the Taylor series of the phi-functions."""
+    tau = 0.1
+    c = O.cox_matthews_coefficients(np.array([0.0, 1e-3]), tau)
+    assert c["R13"][0] == 1.0 and c["Q13"][0] == 1.0
+    for k, v in (("phi", tau / 2), ("phi1", tau / 6), ("phi2", tau / 3), ("phi3", tau / 6)):
+        assert c[k][0] == pytest.approx(v, rel=1e-14), k
+    L = 1e-3   # series to O(L^2) (alpha = 1/6 - z/6 + 3z^2/40 ..., z = -L) from e^z expanded by hand
+    assert c["phi1"][1] == pytest.approx(tau * (1 / 6 - L / 6 + 3 * L * L / 40), rel=1e-9)
+    assert c["phi2"][1] == pytest.approx(2 * tau * (1 / 6 - L / 12 + L * L / 40), rel=1e-9)
+    assert c["phi3"][1] == pytest.approx(tau * (1 / 6 + 0 * L - L * L / 120), rel=1e-9)
+
+
+def test_cox_matthews_single_eigenmode_decays_exactly():
+    """f = 0: each eigen-coefficient decays by exactly exp(-kappa Lambda^{alpha/2} t)."""
+    N, M, tau = 16, 7, 0.2
+    g = O.Grid((N, N), (0.0, 0.0), (2.0, 2.0))
+    f, J = O.linear(0.0)
+    for bc in O.BCS:
+        prob = O.Problem(g, bc, [1.7], [0.3], tau, f, dreaction=J, nspecies=1)
+        s = O.ETDRK4P13(prob, scheme="cox_matthews")
+        u0 = np.random.default_rng(3).standard_normal(g.shape(bc))
+        uM = s.run([u0], 0.0, M)[0]
+        lam = s.sp.Lambda_frac(1.7)
+        expect = s.sp.forward(u0) * np.exp(-0.3 * lam * tau * M)
+        np.testing.assert_allclose(s.sp.forward(uM), expect, atol=1e-12 * np.abs(expect).max())
+
+
+def test_cox_matthews_is_exact_for_a_constant_source():
+    """f(u) = c (constant): the exact solution of u_t = -K u + c is reached in one step."""
+    N, tau, cval = 12, 0.3, 0.7
+    g = O.Grid((N, N), (0.0, 0.0), (1.0, 1.5))
+
+    def f(w, t):
+        return [np.full_like(w[0], cval)]
+
+    for bc in O.BCS:
+        prob = O.Problem(g, bc, [1.5], [0.8], tau, f, nspecies=1)
+        s = O.ETDRK4P13(prob, scheme="cox_matthews")
+        u0 = np.random.default_rng(5).standard_normal(g.shape(bc))
+        u1 = s.run([u0], 0.0, 1)[0]
+        L = s.L[0]
+        Lsafe = np.where(L > 0, L, 1.0)
+        gain = np.where(L > 0, tau * (1 - np.exp(-L)) / Lsafe, tau)
+        expect = np.exp(-L) * s.sp.forward(u0) + gain * s.sp.forward(np.full(g.shape(bc), cval))
+        np.testing.assert_allclose(s.sp.forward(u1), expect, atol=1e-12 * np.abs(expect).max())
+
+
+def test_cox_matthews_and_p13_agree_to_fifth_order_in_l():
+    """The schemes differ only through e^{-L} versus R13(L) = e^{-L} + O(L^5) per step."""
+    tau = 1.0
+    d = []
+    for L in (0.02, 0.04):
+        a, b = O.cox_matthews_coefficients(np.array([L]), tau), O.p13_coefficients(np.array([L]), tau)
+        d.append(abs(a["R13"][0] - b["R13"][0]))
+    assert d[1] / d[0] == pytest.approx(32.0, rel=0.05)
