@@ -48,7 +48,7 @@ extern "C" {
 #define SFRD_OK            0
 #define SFRD_EINVAL       -1  /* bad argument: alpha not in (1,2], kappa < 0, dt <= 0, N < 2, ... */
 #define SFRD_EUNSUPPORTED -2  /* valid problem outside what this build handles (length not
-                                 {2,3,5}-smooth, FFT length > 1024, dim not 2 or 3, a field
+                                 {2,3,5}-smooth, FFT length > 1024, a field
                                  array of 2^32 elements or more, ...) */
 #define SFRD_ENOWS        -3  /* workspace missing, too small or not bound */
 #define SFRD_ECUDA        -4  /* a CUDA runtime call failed; see sfrd_last_error() */
@@ -77,6 +77,8 @@ extern "C" {
  *                      f_u = c1 U^2/V - c2 U,   f_v = c3 U^2 - c4 V
  *   HUXLEY_MMS         Example 2 (Section 5.1): u(1-u)(u-1) + the manufactured source
  *                      of u = t^alpha cos^3(2 pi x) cos^3(2 pi y); 1 species, 2D.
+ *   FISHER_MMS         Example 1 (Section 5.1): u - u^2 + the manufactured source of
+ *                      u = e^{-t} sin^3(2 pi x) (one kappa); 1 species, 1D.
  * For SCHNAKENBERG and GIERER_MEINHARDT, U = u + offset[0], V = v + offset[1]:
  * the solver integrates the perturbation about (offset[0], offset[1]); with
  * Dirichlet BCs the boundary condition applies to that perturbation. */
@@ -87,11 +89,12 @@ extern "C" {
 #define SFRD_REACT_SCHNAKENBERG      4
 #define SFRD_REACT_GIERER_MEINHARDT  5
 #define SFRD_REACT_HUXLEY_MMS        6
+#define SFRD_REACT_FISHER_MMS        7
 
 typedef struct sfrd_plan_s* sfrd_plan_t;
 
 typedef struct {
-    int32_t dim;      /* 2 or 3 */
+    int32_t dim;      /* 1, 2 or 3 */
     int64_t N[3];     /* intervals per axis (x, y, z); unused entries ignored */
     double  lo[3];
     double  hi[3];

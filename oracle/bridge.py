@@ -34,6 +34,9 @@ def reaction_fns(cfg):
 
 def problem(cfg):
     g = O.Grid(tuple(cfg["N"]), tuple(cfg["lo"]), tuple(cfg["hi"]))
+    if cfg["reaction"]["kind"] == "fisher_mms":     # Example 1 (needs the grid)
+        f, _ = O.fisher_mms(g, cfg["kappa"][0], cfg["alpha"][0])
+        return O.Problem(g, cfg["bc"], list(cfg["alpha"]), list(cfg["kappa"]), cfg["dt"], f, nspecies=1)
     f, J, _ = reaction_fns(cfg)
     return O.Problem(g, cfg["bc"], list(cfg["alpha"]), list(cfg["kappa"]), cfg["dt"], f,
                      dreaction=J, nspecies=len(cfg["alpha"]))

@@ -27,7 +27,7 @@ ERRORS = {-1: "EINVAL", -2: "EUNSUPPORTED", -3: "ENOWS", -4: "ECUDA", -5: "ENONF
 BC = {"periodic": 0, "dirichlet": 1, "neumann": 2}
 DTYPE = {"f64": 0, "f32": 1}
 REACTION = {"none": 0, "linear": 1, "fhn": 2, "gray_scott": 3, "schnakenberg": 4,
-            "gierer_meinhardt": 5, "huxley_mms": 6}
+            "gierer_meinhardt": 5, "huxley_mms": 6, "fisher_mms": 7}
 COEFFICIENTS = ("R13", "Q13", "phi", "phi1", "phi2", "phi3")
 COEF_MODE = {"stored": 0, "rational": 1}
 SCHEME = {"p13": 0, "cox_matthews": 1}

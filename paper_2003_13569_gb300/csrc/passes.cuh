@@ -650,6 +650,82 @@ static cudaError_t run_x(const Plan& p, int mode, const Arr<T>& in, const Arr<T>
     return launch_x<T>(p, mode, a, grid, s);
 }
 
+// ---- 1D: the spectral combination as a pointwise pass ------------------------------------
+//
+// With one axis the transform of the x pass is the whole transform: after the x pass (T, f, T)
+// the work array holds F(f) in spectral space, and the stage combination (Algorithm 1) is pointwise;
+// its result times 1/C is what the next x pass transforms back.  mode T0 (load): U <- W, W <- W/C;
+// TA/TB/TC/TD as in the slow-axis passes with F = W.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) combine1d_kernel(const ColArgs<T> a, long long total, long long plane) {
+    const T invC = (T)a.invC, tau = (T)a.tau;
+    T* W = const_cast<T*>(a.in);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(e / plane);                 // species
+        const T F = W[e];
+        T Q = 0, ph = 0, R = 0, p1 = 0, p2 = 0, p3 = 0;
+        if (MODE != MODE_T0) {
+            if (a.CL) {
+                const T L = (T)a.cl_mult[h] * a.CL[h ? e - plane + a.clB : e];
+                if (MODE == MODE_TD) p13_rphi<T>(L, tau, R, p1, p2, p3);
+                else p13_qphi<T>(L, tau, Q, ph);
+            } else if (MODE == MODE_TD) {
+                R = a.CR[4 * e]; p1 = a.CR[4 * e + 1]; p2 = a.CR[4 * e + 2]; p3 = a.CR[4 * e + 3];
+            } else {
+                Q = a.CQ[2 * e]; ph = a.CQ[2 * e + 1];
+            }
+        }
+        T out;
+        if (MODE == MODE_T0) {
+            a.U[e] = F;
+            out = F;
+        } else if (MODE == MODE_TA || MODE == MODE_TB) {
+            if (MODE == MODE_TA) a.F1[e] = F; else a.F2[e] = F;
+            out = Q * a.U[e] + ph * F;
+        } else if (MODE == MODE_TC) {
+            a.F3[e] = F;
+            const T f1 = a.F1[e];
+            const T ah = Q * a.U[e] + ph * f1;
+            out = Q * ah + ph * ((T)2 * F - f1);
+        } else {
+            const T un = R * a.U[e] + p1 * a.F1[e] + p2 * (a.F2[e] + a.F3[e]) + p3 * F;
+            if (a.F4) a.F4[e] = F;
+            a.U[e] = un;
+            out = un;
+        }
+        W[e] = out * invC;
+    }
+    if (MODE == MODE_TD && blockIdx.x == 0 && threadIdx.x == 0) a.clock->k += 1;
+}
+
+template <typename T>
+static cudaError_t run_combine1d(const Plan& p, int mode, const Arr<T>& W, cudaStream_t s) {
+    dim3 grid;
+    ColArgs<T> a = col_args<T>(p, 0, W, W, 1.0, grid);
+    const long long total = (long long)p.S * p.plane;
+    const int blocks = (int)((total + kThreads - 1) / kThreads < 1024 ? (total + kThreads - 1) / kThreads : 1024);
+    switch (mode) {
+        case MODE_T0: combine1d_kernel<T, MODE_T0><<<blocks, kThreads, 0, s>>>(a, total, p.plane); break;
+        case MODE_TA: combine1d_kernel<T, MODE_TA><<<blocks, kThreads, 0, s>>>(a, total, p.plane); break;
+        case MODE_TB: combine1d_kernel<T, MODE_TB><<<blocks, kThreads, 0, s>>>(a, total, p.plane); break;
+        case MODE_TC: combine1d_kernel<T, MODE_TC><<<blocks, kThreads, 0, s>>>(a, total, p.plane); break;
+        default: combine1d_kernel<T, MODE_TD><<<blocks, kThreads, 0, s>>>(a, total, p.plane); break;
+    }
+    return cudaGetLastError();
+}
+
+// out (internal layout) = scale * in (dense [S][n]) for the 1D inverse transform entry point.
+template <typename T>
+__global__ void scale1d_kernel(const T* __restrict__ in, T* __restrict__ out, int n, int pitch, int S, double scale) {
+    const long long total = (long long)S * pitch;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(e % pitch), sp = (int)(e / pitch);
+        out[e] = x < n ? (T)scale * in[(long long)sp * n + x] : (T)0;
+    }
+}
+
 // One step.  With `ev` non-null, event ev[i] is recorded before launch i and
 // ev[i+1] after it, and kind[i] receives the pass kind (PassKind).  With `sv`
 // non-null the stage spectra and physical stage values are written to the
@@ -673,6 +749,20 @@ static cudaError_t step_impl(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind
         return e;
     };
     for (int st = 0; st < 4; ++st) {
+        if (p.dim == 1) {
+            SFRD_TRY(mark(PASS_X));
+            {
+                dim3 grid;
+                XArgs<T> a = x_args<T>(p, W, W, p.pitch, frac[st], grid);
+                if (sv) a.save = static_cast<T*>(sv->stage[st]);
+                SFRD_TRY(launch_x<T>(p, MODE_REACT, a, grid, s));
+            }
+            SFRD_TRY(done());
+            SFRD_TRY(mark(PASS_SLOW_A + st));
+            SFRD_TRY(run_combine1d<T>(p, MODE_TA + st, W, s));
+            SFRD_TRY(done());
+            continue;
+        }
         if (p.dim == 3) {
             SFRD_TRY(mark(PASS_MID));
             SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W, W, 1.0, s));
@@ -723,6 +813,7 @@ cudaError_t launch_load(Plan& p, const void* u0, cudaStream_t s) {
     const Arr<T> W = internal_arr<T>(p, p.off_W);
     const int slow = p.dim == 3 ? 2 : 1;
     SFRD_TRY(run_x<T>(p, MODE_PLAIN, dense_arr<T>(p, u0), W, p.pitch, 0.0, s));
+    if (p.dim == 1) return run_combine1d<T>(p, MODE_T0, W, s);
     if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W, W, 1.0, s));
     return run_col<T>(p, slow, MODE_T0, W, W, 1.0, s);
 }
@@ -742,6 +833,7 @@ template <typename T>
 cudaError_t launch_forward(Plan& p, const void* u, void* uhat, cudaStream_t s) {
     const Arr<T> W2 = internal_arr<T>(p, p.off_W2);
     const int slow = p.dim == 3 ? 2 : 1;
+    if (p.dim == 1) return run_x<T>(p, MODE_PLAIN, dense_arr<T>(p, u), dense_arr<T>(p, uhat), 0, 0.0, s);
     SFRD_TRY(run_x<T>(p, MODE_PLAIN, dense_arr<T>(p, u), W2, p.pitch, 0.0, s));
     if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
     return run_col<T>(p, slow, MODE_PLAIN, W2, dense_arr<T>(p, uhat), 1.0, s);
@@ -754,6 +846,12 @@ cudaError_t launch_inverse(Plan& p, const void* uhat, void* u, cudaStream_t s) {
     double C = 1.0;
     for (int k = 0; k < p.dim; ++k) C *= (p.bc == SFRD_BC_PERIODIC) ? (double)p.Nint[k] : 0.5 * (double)p.Nint[k];
     SFRD_TRY(cudaMemsetAsync(p.ws + p.off_W2, 0, (size_t)p.S * p.plane * sizeof(T), s));
+    if (p.dim == 1) {
+        scale1d_kernel<T><<<64, kThreads, 0, s>>>(static_cast<const T*>(uhat), wsT<T>(p, p.off_W2), p.n[0], p.pitch,
+                                                   p.S, 1.0 / C);
+        SFRD_TRY(cudaGetLastError());
+        return run_x<T>(p, MODE_PLAIN, W2, dense_arr<T>(p, u), 0, 0.0, s);
+    }
     SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, dense_arr<T>(p, uhat), W2, 1.0 / C, s));
     if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
     return run_x<T>(p, MODE_PLAIN, W2, dense_arr<T>(p, u), 0, 0.0, s);

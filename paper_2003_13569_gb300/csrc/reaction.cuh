@@ -70,6 +70,15 @@ __device__ __forceinline__ T react1(const ReactDev& re, T u, double x, double y,
             const double src = dta * g + ta * Phi - w * (1.0 - w) * (w - 1.0);
             return u * ((T)1 - u) * (u - (T)1) + (T)src;
         }
+        case SFRD_REACT_FISHER_MMS: {
+            // Example 1: exact solution e^{-t} sin^3(2 pi x); p = [k1, k3] with the fractional
+            // source (kappa/4) e^{-t} (k1 sin 2 pi x - k3 sin 6 pi x), k1 = 3 (2 pi)^alpha, k3 = (6 pi)^alpha
+            // folded in (p0 = kappa/4 k1, p1 = kappa/4 k3)
+            const double s1 = sinpi(2.0 * x), s3 = sinpi(6.0 * x);
+            const double e = exp(-t), sc = s1 * s1 * s1;
+            const double src = -2.0 * e * sc + e * (re.p[0] * s1 - re.p[1] * s3) + e * e * sc * sc;
+            return u - u * u + (T)src;
+        }
         default:
             return 0;
     }
@@ -139,6 +148,8 @@ __device__ __forceinline__ T react1_vjp(const ReactDev& re, T u, T y, double w, 
             return (T)re.p[0] * y;
         case SFRD_REACT_HUXLEY_MMS:
             return ((T)1 - u) * ((T)3 * u - (T)1) * y;   // d/du [u (1-u)(u-1)]; the source has no u
+        case SFRD_REACT_FISHER_MMS:
+            return ((T)1 - (T)2 * u) * y;
         default:
             return 0;
     }

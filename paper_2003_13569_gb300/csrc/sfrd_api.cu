@@ -36,7 +36,7 @@ cudaError_t launch_set_clock(Plan& p, double t0, cudaStream_t s, long long k0) {
     return cudaGetLastError();
 }
 
-int kernels_per_step(const Plan& p) { return p.dim == 3 ? 16 : 8; }
+int kernels_per_step(const Plan& p) { return p.dim == 3 ? 16 : 8; }   // 1D: x pass + combine per stage
 
 // cos and sin of 2 pi k / M with exact octant reduction in long double.
 static void cos_sin_2pi(long long k, long long M, double& c, double& s) {
@@ -164,10 +164,12 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
         case SFRD_REACT_HUXLEY_MMS:
             if (S != 1 || g->dim != 2) return SFRD_EINVAL;
             break;
+        case SFRD_REACT_FISHER_MMS:
+            if (S != 1 || g->dim != 1) return SFRD_EINVAL;
+            break;
         default:
             return SFRD_EINVAL;
     }
-    if (g->dim == 1) return SFRD_EUNSUPPORTED;
 
     Plan* p = new (std::nothrow) Plan();
     if (!p) return SFRD_EINVAL;
@@ -227,6 +229,11 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
     for (int i = 0; i < 8; ++i) p->re.p[i] = re->p[i];
     p->re.off[0] = re->offset[0];
     p->re.off[1] = re->offset[1];
+    if (re->kind == SFRD_REACT_FISHER_MMS) {
+        const double a = alpha[0], k = kappa[0];
+        p->re.p[0] = k / 4.0 * 3.0 * std::pow(2.0 * M_PI, a);
+        p->re.p[1] = k / 4.0 * std::pow(6.0 * M_PI, a);
+    }
     if (re->kind == SFRD_REACT_HUXLEY_MMS) {
         const double a = alpha[0], k = kappa[0], pi2 = M_PI * M_PI;
         p->re.p[0] = a;
@@ -386,6 +393,7 @@ AdjLayout adj_layout(const Plan& p, int64_t nsteps, int64_t K) {
 }
 
 static bool adjoint_capable(const Plan& p) {
+    if (p.dim == 1) return false;
     if (p.coef_mode == SFRD_COEF_RATIONAL) return false;   // the adjoint differentiates the stored arrays
     if (p.scheme != SFRD_SCHEME_P13) return false;         // ... of the Padé(1,3) scheme
     for (int d = 0; d < p.dim; ++d)

@@ -51,6 +51,7 @@ int sfrd_batch_plan(sfrd_batch_t* out, int64_t count, const sfrd_grid* grids, co
     if (!out) return SFRD_EINVAL;
     *out = nullptr;
     if (count < 1 || !grids || !bcs || !alpha || !kappa || !reaction) return SFRD_EINVAL;
+    if (grids[0].dim == 1) return SFRD_EUNSUPPORTED;   // batched passes are the 2D/3D ones
     sfrd_batch_s* h = new (std::nothrow) sfrd_batch_s();
     if (!h) return SFRD_EINVAL;
     BatchPlan& b = h->b;

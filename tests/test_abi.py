@@ -84,7 +84,8 @@ def test_valid_plan_reports_sizes(sfrd):
     (dict(N=(14, 16, 1), bc="periodic"), -2),                   # 14 = 2 * 7 is not {2,3,5}-smooth
     (dict(N=(2048, 16, 1), bc="neumann"), -2),                  # beyond both engines' lengths
     (dict(N=(600, 16, 1), bc="neumann"), -2),                   # extension length 1200 > 1024, not a power of 2
-    (dict(dim=1), -2),
+    (dict(dim=4), -1),
+    (dict(reaction="fisher_mms", alpha=(1.5,), kappa=(1.0,)), -1),  # Example 1 is one-dimensional
 ])
 def test_invalid_arguments_are_rejected(sfrd, kw, code):
     with pytest.raises(sfrd.SfrdError) as ei:
