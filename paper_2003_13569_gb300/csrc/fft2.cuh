@@ -190,9 +190,13 @@ struct Eng {
 
     // Pre-processed input z_j of the packed DFT, read from the value buffer.
     static __device__ __forceinline__ C pre(const C* V, int bc_, int j, int c, const C* tws, C& anchor) {
+        return pre_w(V, bc_, j, c, tws[j], anchor);
+    }
+
+    // The same with w = (cos(j pi/N), -sin(j pi/N)) given.
+    static __device__ __forceinline__ C pre_w(const C* V, int bc_, int j, int c, C w, C& anchor) {
         const int bc = bcv(bc_);
         if (bc == SFRD_BC_PERIODIC) return V[j * LD + c];
-        const C w = tws[j];               // (cos(j pi/N), -sin(j pi/N))
         const T s = -w.y;
         if (bc == SFRD_BC_DIRICHLET) {
             if (j == 0) return czero<C>();
@@ -221,7 +225,22 @@ struct Eng {
             const int n2 = g + o * G;
             if (R2 % G == 0 || n2 < R2) {
 #pragma unroll
-                for (int n1 = 0; n1 < R1; ++n1) a[o][n1] = pre(buf, bc, R2 * n1 + n2, c, tws, anchor);
+                if (BCT >= 0) {
+                    // w_j for j = R2 n1 + n2 by rotating w_{n2} (one table read) through the
+                    // compile-time angle R2 n1 pi / N
+                    const C wb = BCT == SFRD_BC_PERIODIC ? czero<C>() : tws[n2];
+                    static_for<0, R1>([&](auto N1) {
+                        constexpr int n1 = decltype(N1)::value;
+                        constexpr T cr = (T)ce_cs2pi(R2 * n1, 2 * N).c, ci = (T)(-ce_cs2pi(R2 * n1, 2 * N).s);
+                        C w;
+                        w.x = wb.x * cr - wb.y * ci;
+                        w.y = wb.x * ci + wb.y * cr;
+                        a[o][n1] = pre_w(buf, bc, R2 * n1 + n2, c, w, anchor);
+                    });
+                } else {
+#pragma unroll
+                    for (int n1 = 0; n1 < R1; ++n1) a[o][n1] = pre(buf, bc, R2 * n1 + n2, c, tws, anchor);
+                }
                 RDft<R1, C>::run(a[o]);
 #pragma unroll
                 for (int k1 = 1; k1 < R1; ++k1) a[o][k1] = cmul(a[o][k1], tws[(n2 * k1) * twstride]);
