@@ -225,10 +225,10 @@ struct Eng {
             const int n2 = g + o * G;
             if (R2 % G == 0 || n2 < R2) {
 #pragma unroll
-                if (BCT >= 0) {
+                {
                     // w_j for j = R2 n1 + n2 by rotating w_{n2} (one table read) through the
                     // compile-time angle R2 n1 pi / N
-                    const C wb = BCT == SFRD_BC_PERIODIC ? czero<C>() : tws[n2];
+                    const C wb = bc == SFRD_BC_PERIODIC ? czero<C>() : tws[n2];
                     static_for<0, R1>([&](auto N1) {
                         constexpr int n1 = decltype(N1)::value;
                         constexpr T cr = (T)ce_cs2pi(R2 * n1, 2 * N).c, ci = (T)(-ce_cs2pi(R2 * n1, 2 * N).s);
@@ -237,9 +237,6 @@ struct Eng {
                         w.y = wb.x * ci + wb.y * cr;
                         a[o][n1] = pre_w(buf, bc, R2 * n1 + n2, c, w, anchor);
                     });
-                } else {
-#pragma unroll
-                    for (int n1 = 0; n1 < R1; ++n1) a[o][n1] = pre(buf, bc, R2 * n1 + n2, c, tws, anchor);
                 }
                 RDft<R1, C>::run(a[o]);
 #pragma unroll
