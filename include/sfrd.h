@@ -201,6 +201,16 @@ int sfrd_load(sfrd_plan_t plan, const void* u0, double t0);
  * t_k + tau/2, t_k + tau).  Launched as a captured CUDA graph.  nsteps >= 0. */
 int sfrd_advance(sfrd_plan_t plan, int64_t nsteps);
 
+/* Failure detection: SFRD_ENONFINITE when the resident spectral state holds a
+ * NaN or an infinity (a blown-up run, or a non-finite initial field), else
+ * SFRD_OK.  One reduction kernel writes a device flag that the host reads back
+ * (synchronises the stream; nothing waits on the device).  With the environment
+ * variable SFRD_DEBUG_CHECKS set (not "0") when the plan is created,
+ * sfrd_advance (and so sfrd_run, sfrd_step) ends with this check and returns
+ * its code.  Errors: SFRD_EINVAL, SFRD_ENOWS, SFRD_ESTATE (nothing loaded),
+ * SFRD_ECUDA. */
+int sfrd_check_finite(sfrd_plan_t plan);
+
 /* Write the resident state to the physical device field u [S][...]
  * (Algorithm 1: u = ifftn(...)).  Does not change the resident state. */
 int sfrd_store(sfrd_plan_t plan, void* u);

@@ -31,7 +31,7 @@ REACTION = {"none": 0, "linear": 1, "fhn": 2, "gray_scott": 3, "schnakenberg": 4
 COEFFICIENTS = ("R13", "Q13", "phi", "phi1", "phi2", "phi3")
 COEF_MODE = {"stored": 0, "rational": 1}
 SCHEME = {"p13": 0, "cox_matthews": 1}
-EXPORTS = ("sfrd_plan", "sfrd_set_coefficients", "sfrd_set_scheme", "sfrd_autotune", "sfrd_batch_autotune", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
+EXPORTS = ("sfrd_plan", "sfrd_set_coefficients", "sfrd_set_scheme", "sfrd_check_finite", "sfrd_autotune", "sfrd_batch_autotune", "sfrd_workspace_bytes", "sfrd_get_info", "sfrd_bind", "sfrd_load", "sfrd_advance",
            "sfrd_store", "sfrd_run", "sfrd_step", "sfrd_run_host", "sfrd_forward", "sfrd_forward_noalloc", "sfrd_inverse",
            "sfrd_coefficients", "sfrd_profile_step", "sfrd_adjoint_workspace_bytes", "sfrd_run_checkpointed",
            "sfrd_adjoint", "sfrd_batch_plan", "sfrd_batch_workspace_bytes", "sfrd_batch_bind", "sfrd_batch_load",
@@ -62,6 +62,7 @@ _lib.sfrd_plan.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(Grid), ctypes.c_in
                            ctypes.POINTER(_D), _D, ctypes.c_int32, ctypes.POINTER(Reaction)]
 _lib.sfrd_set_coefficients.argtypes = [_P, ctypes.c_int32]
 _lib.sfrd_set_scheme.argtypes = [_P, ctypes.c_int32]
+_lib.sfrd_check_finite.argtypes = [_P]
 _lib.sfrd_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
 _lib.sfrd_batch_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
 _lib.sfrd_workspace_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
@@ -262,6 +263,14 @@ class Solver:
         out = self.empty()
         _check(_lib.sfrd_inverse(self.handle, _ptr(uhat), _ptr(out)), "sfrd_inverse")
         return out
+
+    def check_finite(self):
+        """True when the resident state holds only finite values (False: SFRD_ENONFINITE)."""
+        code = _lib.sfrd_check_finite(self.handle)
+        if code == -5:
+            return False
+        _check(code, "sfrd_check_finite")
+        return True
 
     def autotune(self, steps=3):
         """Pick the fastest radix/tile schedule of the shared-memory engine's axes (the resident state

@@ -857,6 +857,25 @@ cudaError_t launch_inverse(Plan& p, const void* uhat, void* u, cudaStream_t s) {
     return run_x<T>(p, MODE_PLAIN, W2, dense_arr<T>(p, u), 0, 0.0, s);
 }
 
+// Sets *flag when any value of the resident spectral state is not finite (the flag is cleared by the
+// caller first).  A spectral value is finite exactly when the run has not blown up or been fed a
+// non-finite field: every transform mixes all values of a line.
+template <typename T>
+__global__ void finite_check_kernel(const T* __restrict__ x, long long n, int* flag) {
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) *flag = 1;
+}
+
+template <typename T>
+cudaError_t launch_finite_check(Plan& p, cudaStream_t s) {
+    int* flag = reinterpret_cast<int*>(p.ws + p.off_flag);
+    SFRD_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    finite_check_kernel<T><<<304, kThreads, 0, s>>>(wsT<T>(p, p.off_U), (long long)p.S * p.plane, flag);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_coef_init(Plan& p, cudaStream_t s) {
     const double* lx = reinterpret_cast<const double*>(p.ws + p.off_lam[0]);
@@ -1036,6 +1055,7 @@ cudaError_t launch_adjoint(Plan& p, double t0, int64_t nsteps, int64_t K, char* 
     template cudaError_t launch_forward<T>(Plan&, const void*, void*, cudaStream_t);         \
     template cudaError_t launch_inverse<T>(Plan&, const void*, void*, cudaStream_t);         \
     template cudaError_t launch_coef_init<T>(Plan&, cudaStream_t);                           \
+    template cudaError_t launch_finite_check<T>(Plan&, cudaStream_t);                        \
     template cudaError_t launch_coef_copy<T>(Plan&, int, void*, cudaStream_t);          \
     template cudaError_t prepare_kernels<T>(const Plan&);                                  \
     template cudaError_t launch_run_checkpointed<T>(Plan&, void*, double, int64_t, int64_t, char*,       \

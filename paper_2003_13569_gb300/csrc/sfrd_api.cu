@@ -126,6 +126,7 @@ static void layout_workspace(Plan* p) {
     }
     p->off_D = take((size_t)S * p->dense * E);
     p->off_clock = take(sizeof(Clock));
+    p->off_flag = take(sizeof(int));
     for (int d = 0; d < 3; ++d) {
         p->off_tw[d] = take((size_t)p->M[d] * 2 * E);
         p->off_perm[d] = take((size_t)p->M[d] * sizeof(int));
@@ -292,6 +293,10 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
         }
     }
 
+    {
+        const char* dbg = std::getenv("SFRD_DEBUG_CHECKS");
+        p->debug_checks = dbg && *dbg && std::strcmp(dbg, "0") != 0;
+    }
     layout_workspace(p);
     *out = p;
     return SFRD_OK;
@@ -475,6 +480,18 @@ static int load(Plan* p, const void* u0, double t0) {
     return SFRD_OK;
 }
 
+// SFRD_ENONFINITE when the resident state holds a NaN or an infinity (synchronises the stream).
+static int check_finite(Plan* p) {
+    if (!p->ws) return SFRD_ENOWS;
+    if (!p->loaded) return SFRD_ESTATE;
+    SFRD_CUDA(p->dtype == SFRD_F32 ? launch_finite_check<float>(*p, p->stream)
+                                   : launch_finite_check<double>(*p, p->stream));
+    int flag = 0;
+    SFRD_CUDA(cudaMemcpyAsync(&flag, p->ws + p->off_flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    SFRD_CUDA(cudaStreamSynchronize(p->stream));
+    return flag ? SFRD_ENONFINITE : SFRD_OK;
+}
+
 static int advance(Plan* p, int64_t nsteps) {
     if (!p->ws) return SFRD_ENOWS;
     if (!p->loaded) return SFRD_ESTATE;
@@ -487,7 +504,7 @@ static int advance(Plan* p, int64_t nsteps) {
     } else {
         for (int64_t i = 0; i < nsteps; ++i) SFRD_CUDA(step_direct(p, p->stream));
     }
-    return SFRD_OK;
+    return p->debug_checks ? check_finite(p) : SFRD_OK;
 }
 
 static int store(Plan* p, void* u) {
@@ -654,6 +671,11 @@ int sfrd_load(sfrd_plan_t plan, const void* u0, double t0) {
 int sfrd_advance(sfrd_plan_t plan, int64_t nsteps) {
     if (!plan) return SFRD_EINVAL;
     return sfrd::advance(&plan->p, nsteps);
+}
+
+int sfrd_check_finite(sfrd_plan_t plan) {
+    if (!plan) return SFRD_EINVAL;
+    return sfrd::check_finite(&plan->p);
 }
 
 int sfrd_store(sfrd_plan_t plan, void* u) {

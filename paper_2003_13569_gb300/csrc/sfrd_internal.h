@@ -154,6 +154,8 @@ struct Plan {
     bool cl_shared = false;     // rational mode: one plane tau Lambda^{alpha/2} for both species
     int sched_rule = 0;         // radix-order rule of the shared-memory engine (apply_schedule)
     int scheme = 0;             // SFRD_SCHEME_P13 or SFRD_SCHEME_COX_MATTHEWS
+    bool debug_checks = false;  // SFRD_DEBUG_CHECKS set at plan creation: check the state after advance
+    size_t off_flag = 0;        // device int written by the non-finite check
     size_t off_CL = 0;
     size_t off_tw[3] = {0, 0, 0}, off_perm[3] = {0, 0, 0}, off_lam[3] = {0, 0, 0};
     size_t ws_bytes = 0;
@@ -174,6 +176,7 @@ template <typename T> cudaError_t launch_store(Plan& p, void* u, cudaStream_t s)
 template <typename T> cudaError_t launch_forward(Plan& p, const void* u, void* uhat, cudaStream_t s);
 template <typename T> cudaError_t launch_inverse(Plan& p, const void* uhat, void* u, cudaStream_t s);
 template <typename T> cudaError_t launch_coef_init(Plan& p, cudaStream_t s);
+template <typename T> cudaError_t launch_finite_check(Plan& p, cudaStream_t s);
 template <typename T> cudaError_t launch_coef_copy(Plan& p, int which, void* out, cudaStream_t s);
 template <typename T> cudaError_t prepare_kernels(const Plan& p);
 

@@ -148,3 +148,11 @@ def test_scheme_selection_on_the_host(sfrd):
     assert lib.sfrd_set_coefficients(h, 1) == 0
     assert lib.sfrd_set_scheme(h, 1) == -2                  # and the other way round
     lib.sfrd_destroy(h)
+
+
+def test_finite_check_needs_a_bound_loaded_plan(sfrd):
+    lib = sfrd.lib()
+    h = _plan(sfrd)
+    assert lib.sfrd_check_finite(h) == -3
+    assert lib.sfrd_check_finite(None) == -1
+    lib.sfrd_destroy(h)
