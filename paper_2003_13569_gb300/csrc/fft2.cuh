@@ -239,8 +239,25 @@ struct Eng {
                     });
                 }
                 RDft<R1, C>::run(a[o]);
+                if (R1 <= 16) {
+                    // omega_N^{n2 k1} = (omega_N^{4 n2})^{k1 / 4} (omega_N^{n2})^{k1 % 4}: two table reads
+                    C pw[4], qw[R1 / 4];
+                    pw[1] = tws[n2 * twstride];
+                    pw[2] = cmul(pw[1], pw[1]);
+                    pw[3] = cmul(pw[2], pw[1]);
+                    if (R1 / 4 > 1) qw[1] = tws[4 * n2 * twstride];
+                    if (R1 / 4 > 2) qw[2] = cmul(qw[1], qw[1]);
+                    if (R1 / 4 > 3) qw[3] = cmul(qw[2], qw[1]);
 #pragma unroll
-                for (int k1 = 1; k1 < R1; ++k1) a[o][k1] = cmul(a[o][k1], tws[(n2 * k1) * twstride]);
+                    for (int k1 = 1; k1 < R1; ++k1) {
+                        const int qq = k1 / 4, r = k1 % 4;
+                        if (qq > 0) a[o][k1] = cmul(a[o][k1], qw[qq]);
+                        if (r > 0) a[o][k1] = cmul(a[o][k1], pw[r]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k1 = 1; k1 < R1; ++k1) a[o][k1] = cmul(a[o][k1], tws[(n2 * k1) * twstride]);
+                }
             }
         }
         red2[g * CC + c] = anchor;
