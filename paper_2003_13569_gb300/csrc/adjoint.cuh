@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE_TA>())) adj_c
     const C* tw = static_cast<const C*>(ax.tw);
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
     for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);
-    const int xA = blockIdx.x * a.xw + c, xB = xA + a.bshift;
+    const int xA = blockIdx.x * a.xw + c * a.cstride, xB = xA + a.bshift;
     const int other = blockIdx.y;
     const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
     const long long base = (long long)other * a.in_sOther + xA;

@@ -63,7 +63,7 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int bx, int by, un
     constexpr int G = kThreads / CC;
     const int tid = threadIdx.x, c = tid % CC, grp = tid / CC;
     const AxisDev& ax = a.ax;
-    const int xA = bx * a.xw + c;
+    const int xA = bx * a.xw + c * a.cstride;
     const int xB = xA + a.bshift;
     const long long other = by;
 
@@ -514,6 +514,12 @@ static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>&
     a.xw = two ? cc : 2 * cc;
     a.in_offB = two ? in.plane : cc;
     a.out_offB = two ? out.plane : cc;
+    a.cstride = 1;
+    if (species_rows) {   // lines A and B of a lane: the adjacent columns x, x + 1 (one 2-element access)
+        a.bshift = 1;
+        a.in_offB = a.out_offB = 1;
+        a.cstride = 2;
+    }
     int gy = 1;
     if (d == 2) {          // z in 3D: blockIdx.y = y
         a.in_sAxis = (long long)ny * in.pitch;

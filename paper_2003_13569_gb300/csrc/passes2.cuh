@@ -56,7 +56,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     const C* tw = static_cast<const C*>(ax.tw);
     const int twstride = bc == SFRD_BC_PERIODIC ? 1 : 2;
     for (int i = tid; i < N * twstride; i += kThreads) tws[i] = __ldg(tw + i);   // visible after the first barrier
-    const int xA = bx * a.xw + c, xB = xA + a.bshift;
+    const int xA = bx * a.xw + c * a.cstride, xB = xA + a.bshift;
     // Element indices: one 64-bit tile origin per thread, then 32-bit offsets (every array of the
     // pass holds fewer than 2^32 elements; checked when the plan is made).
     const size_t org_in = (size_t)by * (size_t)a.in_sOther + (size_t)xA;
@@ -85,6 +85,30 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
             const int i = (w * RPI + sub) + r * NW * RPI;
             if (i < n) dst[2 * i * LD] = v[r];
         }
+    } else if (MODE == MODE_PLAIN && a.cstride == 2) {
+        // lines A and B are the adjacent columns x, x + 1: one 2-element load per row where aligned
+        constexpr int NL = (E::ROWS + G - 1) / G;
+        const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
+        const T* pA = a.in + org_in;
+        const bool vec = okB && ((a.in_sAxis | a.in_sOther) & 1) == 0 &&
+                         (reinterpret_cast<uintptr_t>(a.in) % sizeof(C)) == 0;
+        C z[NL];
+#pragma unroll
+        for (int t = 0; t < NL; ++t) {
+            const int i = g + t * G;
+            const unsigned o = (unsigned)i * s_in;
+            if (i < n && vec) {
+                z[t] = *reinterpret_cast<const C*>(pA + o);
+            } else {
+                z[t].x = (okA && i < n) ? pA[o] : (T)0;
+                z[t].y = (okB && i < n) ? pA[o + 1] : (T)0;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < NL; ++t) {
+            const int i = g + t * G;
+            if (i < n) buf[i * LD + c] = z[t];
+        }
     } else {
         // all loads of this thread issued before any shared-memory store
         constexpr int NL = (E::ROWS + G - 1) / G;
@@ -108,6 +132,27 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     __syncthreads();
     E::forward(buf, red2, bc, tws, twstride, c, g);
 
+    if (MODE == MODE_PLAIN && a.cstride == 2) {
+        // adjacent columns: one 2-element store per output where aligned
+        const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
+        T* qA = a.out + org_out;
+        const bool vec = okB && ((a.out_sAxis | a.out_sOther) & 1) == 0 &&
+                         (reinterpret_cast<uintptr_t>(a.out) % sizeof(C)) == 0;
+        const T sc = (T)a.scale;
+        E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
+            const unsigned o = (unsigned)i * s_out;
+            if (vec) {
+                C w;
+                w.x = v.x * sc;
+                w.y = v.y * sc;
+                *reinterpret_cast<C*>(qA + o) = w;
+            } else {
+                if (okA) qA[o] = v.x * sc;
+                if (okB) qA[o + 1] = v.y * sc;
+            }
+        });
+        return;
+    }
     if (MODE == MODE_PLAIN) {
         const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
         T* qA = a.out + org_out;

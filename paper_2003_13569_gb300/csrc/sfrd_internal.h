@@ -101,6 +101,8 @@ struct ColArgs {
     const T* CL;
     double cl_mult[2];
     long long clB;
+    int cstride;          // x distance between the tile columns of neighbouring lanes (2: lines A and B
+                          // are the adjacent columns x, x + 1 of one array, read and written as pairs)
 };
 
 template <typename T>
