@@ -494,9 +494,19 @@ static Arr<T> dense_arr(const Plan& p, const void* ptr) {
     return Arr<T>{static_cast<const T*>(ptr), p.n[0], p.dense, p.n[0]};
 }
 
+// pair_grid: for a slow-axis pass of an FP32 two-species plan on the register engine with internal
+// arrays and stored coefficients, the lines A and B are the adjacent columns x, x + 1 of one species
+// and the species is blockIdx.z (the slow-axis kernels then read and write element pairs).
+template <typename T>
+static bool use_pair_grid(const Plan& p, int d, const Arr<T>& in, const Arr<T>& out) {
+    return sizeof(T) == 4 && p.S == 2 && p.v2[d] && p.coef_mode == SFRD_COEF_STORED && d == (p.dim == 3 ? 2 : 1) &&
+           in.pitch % 4 == 0 && out.pitch % 4 == 0 && in.xlim == in.pitch && out.xlim == out.pitch;
+}
+
 // Strided pass along axis d (1 = y, 2 = z) from array `in` to `out`.
 template <typename T>
-static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>& out, double scale, dim3& grid) {
+static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>& out, double scale, dim3& grid,
+                           bool pair_grid = false) {
     ColArgs<T> a{};
     const int ny = p.n[1];
     a.in = in.ptr;
@@ -515,10 +525,17 @@ static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>&
     a.in_offB = two ? in.plane : cc;
     a.out_offB = two ? out.plane : cc;
     a.cstride = 1;
-    if (species_rows) {   // lines A and B of a lane: the adjacent columns x, x + 1 (one 2-element access)
+    a.in_sp = a.out_sp = 0;
+    const bool pairs = pair_grid && use_pair_grid<T>(p, d, in, out);
+    if (species_rows || pairs) {   // lines A and B of a lane: the adjacent columns x, x + 1 (one 2-element access)
         a.bshift = 1;
+        a.xw = 2 * cc;
         a.in_offB = a.out_offB = 1;
         a.cstride = 2;
+    }
+    if (pairs) {
+        a.in_sp = in.plane;
+        a.out_sp = out.plane;
     }
     int gy = 1;
     if (d == 2) {          // z in 3D: blockIdx.y = y
@@ -573,7 +590,7 @@ static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>&
     }
     a.tau = p.dt;
     const int xlim = in.xlim > out.xlim ? in.xlim : out.xlim;
-    grid = dim3((xlim + a.xw - 1) / a.xw, gy, 1);
+    grid = dim3((xlim + a.xw - 1) / a.xw, gy, pairs ? p.S : 1);
     return a;
 }
 
@@ -790,7 +807,7 @@ static cudaError_t step_impl(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind
         SFRD_TRY(mark(PASS_SLOW_A + st));
         {
             dim3 grid;
-            ColArgs<T> a = col_args<T>(p, slow, W, W, 1.0, grid);
+            ColArgs<T> a = col_args<T>(p, slow, W, W, 1.0, grid, true);
             if (sv) {
                 a.F1 = static_cast<T*>(sv->F[0]);
                 a.F2 = static_cast<T*>(sv->F[1]);

@@ -39,8 +39,11 @@ __device__ __forceinline__ int unknowns(int n_runtime) {
 }
 
 // RAT: the combination evaluates the coefficients from L (rational-coefficient mode).
-template <typename T, int N, int MODE, int BCT = -1, bool RAT = false>
-__device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, unsigned char* smem_raw) {
+// PAIR (FP32 slow-axis stage passes): lines A and B are the adjacent columns x, x + 1 of the species
+// bz (ColArgs::cstride == 2, internal arrays), so every element access of the combination is one
+// 8-byte pair (16 bytes for the coefficient pairs, 2 x 16 for the quads).
+template <typename T, int N, int MODE, int BCT = -1, bool RAT = false, bool PAIR = false>
+__device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, unsigned char* smem_raw, int bz = 0) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N, BCT>::E;
     using C = typename E::C;
@@ -59,11 +62,29 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     const int xA = bx * a.xw + c * a.cstride, xB = xA + a.bshift;
     // Element indices: one 64-bit tile origin per thread, then 32-bit offsets (every array of the
     // pass holds fewer than 2^32 elements; checked when the plan is made).
-    const size_t org_in = (size_t)by * (size_t)a.in_sOther + (size_t)xA;
-    const size_t org_out = (size_t)by * (size_t)a.out_sOther + (size_t)xA;
+    const size_t org_in = (size_t)by * (size_t)a.in_sOther + (size_t)xA + (size_t)bz * (size_t)a.in_sp;
+    const size_t org_out = (size_t)by * (size_t)a.out_sOther + (size_t)xA + (size_t)bz * (size_t)a.out_sp;
     const unsigned s_in = (unsigned)a.in_sAxis, s_out = (unsigned)a.out_sAxis;
 
-    if (MODE == MODE_PLAIN && a.bshift == CC && a.in_offB == (long long)CC) {
+    if constexpr (PAIR) {
+        // element pairs (internal arrays, even pitch: x < pitch implies x + 1 < pitch; 8-byte aligned);
+        // the lanes of the last tile beyond the pitch hold zeros and store nothing
+        constexpr int NL = (E::ROWS + G - 1) / G;
+        const bool okx = xA < a.in_xlim;
+        const T* pA = a.in + org_in;
+        C z[NL];
+#pragma unroll
+        for (int t = 0; t < NL; ++t) {
+            const int i = g + t * G;
+            z[t] = czero<C>();
+            if (okx && i < n) z[t] = *reinterpret_cast<const C*>(pA + (unsigned)i * s_in);
+        }
+#pragma unroll
+        for (int t = 0; t < NL; ++t) {
+            const int i = g + t * G;
+            if (i < n) buf[i * LD + c] = z[t];
+        }
+    } else if (MODE == MODE_PLAIN && a.bshift == CC && a.in_offB == (long long)CC) {
         // lines A and B are the columns x and x + CC of one array: a tile row is 2 CC consecutive
         // values, read by one warp instruction (LW lanes per row) and stored to the .x (A) or .y (B)
         // halves of the row; all loads of this thread are issued before any shared-memory store
@@ -185,7 +206,32 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                 const unsigned i = eA + (h ? eoB : 0u);
                 // read-only inputs through the non-coherent path (every element is read once,
                 // before its own update); coefficient pairs and quads as single vector loads
-                if (RAT) {
+                if constexpr (PAIR) {
+                    if (h || !ok[0]) continue;   // both lines at once
+                    if (MODE == MODE_TA || MODE == MODE_TB || MODE == MODE_TC) {
+                        const float4 q = __ldg(reinterpret_cast<const float4*>(a.CQ + 2 * (size_t)eA));
+                        const float2 u = __ldg(reinterpret_cast<const float2*>(a.U + eA));
+                        ld[slot][0][0] = q.x; ld[slot][0][1] = q.y; ld[slot][1][0] = q.z; ld[slot][1][1] = q.w;
+                        ld[slot][0][2] = u.x; ld[slot][1][2] = u.y;
+                        if (MODE == MODE_TC) {
+                            const float2 f1 = __ldg(reinterpret_cast<const float2*>(a.F1 + eA));
+                            ld[slot][0][3] = f1.x; ld[slot][1][3] = f1.y;
+                        }
+                    } else if (MODE == MODE_TD) {
+                        const float4 r0 = __ldg(reinterpret_cast<const float4*>(a.CR + 4 * (size_t)eA));
+                        const float4 r1 = __ldg(reinterpret_cast<const float4*>(a.CR + 4 * (size_t)eA) + 1);
+                        const float2 u = __ldg(reinterpret_cast<const float2*>(a.U + eA));
+                        const float2 f1 = __ldg(reinterpret_cast<const float2*>(a.F1 + eA));
+                        const float2 f2 = __ldg(reinterpret_cast<const float2*>(a.F2 + eA));
+                        const float2 f3 = __ldg(reinterpret_cast<const float2*>(a.F3 + eA));
+                        ld[slot][0][4] = r0.x; ld[slot][0][5] = r0.y; ld[slot][0][6] = r0.z; ld[slot][0][7] = r0.w;
+                        ld[slot][1][4] = r1.x; ld[slot][1][5] = r1.y; ld[slot][1][6] = r1.z; ld[slot][1][7] = r1.w;
+                        ld[slot][0][0] = u.x; ld[slot][1][0] = u.y;
+                        ld[slot][0][1] = f1.x; ld[slot][1][1] = f1.y;
+                        ld[slot][0][2] = f2.x; ld[slot][1][2] = f2.y;
+                        ld[slot][0][3] = f3.x; ld[slot][1][3] = f3.y;
+                    }
+                } else if (RAT) {
                     const T Lraw = __ldg(a.CL + eA + (h ? clB : 0u));
                     if (MODE == MODE_TD) {
                         ld[slot][h][4] = Lraw;
@@ -234,6 +280,35 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
             const unsigned eA = e0 + (unsigned)k * s_in;
             const T F[2] = {Fv.x, Fv.y};
             T s[2] = {0, 0};
+            if constexpr (PAIR) {
+                T sv[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const T* L = ld[slot][h];
+                    if (MODE == MODE_TA || MODE == MODE_TB) {
+                        sv[h] = L[0] * L[2] + L[1] * F[h];
+                    } else if (MODE == MODE_TC) {
+                        const T ah = L[0] * L[2] + L[1] * L[3];
+                        sv[h] = L[0] * ah + L[1] * ((T)2 * F[h] - L[3]);
+                    } else {
+                        sv[h] = L[4] * L[0] + L[5] * L[1] + L[6] * (L[2] + L[3]) + L[7] * F[h];
+                    }
+                }
+                const float2 fp = make_float2((float)F[0], (float)F[1]);
+                if (!ok[0]) sv[0] = sv[1] = 0;
+                if (ok[0] && MODE == MODE_TA) *reinterpret_cast<float2*>(a.F1 + eA) = fp;
+                if (ok[0] && MODE == MODE_TB) *reinterpret_cast<float2*>(a.F2 + eA) = fp;
+                if (ok[0] && MODE == MODE_TC) *reinterpret_cast<float2*>(a.F3 + eA) = fp;
+                if (ok[0] && MODE == MODE_TD) {
+                    if (F4) *reinterpret_cast<float2*>(F4 + eA) = fp;
+                    *reinterpret_cast<float2*>(a.U + eA) = make_float2((float)sv[0], (float)sv[1]);
+                }
+                C z;
+                z.x = sv[0] * invC;
+                z.y = sv[1] * invC;
+                buf[k * LD + c] = z;
+                return;
+            }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
@@ -271,7 +346,13 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     }
     __syncthreads();
     E::forward(buf, red2, bc, tws, twstride, c, g);
-    {
+    if constexpr (PAIR) {
+        T* qA = a.out + org_out;
+        const bool okx = xA < a.out_xlim;
+        E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
+            if (okx) *reinterpret_cast<C*>(qA + (unsigned)i * s_out) = v;
+        });
+    } else {
         const bool okA = xA < a.out_xlim, okB = xB < a.out_xlim;
         T* qA = a.out + org_out;
         const unsigned oB = (unsigned)a.out_offB;
@@ -281,13 +362,13 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
             if (okB) qA[o + oB] = v.y;
         });
     }
-    if (MODE == MODE_TD && bx == 0 && by == 0 && threadIdx.x == 0) a.clock->k += 1;
+    if (MODE == MODE_TD && bx == 0 && by == 0 && bz == 0 && threadIdx.x == 0) a.clock->k += 1;
 }
 
-template <typename T, int N, int MODE, int BCT = -1, bool RAT = false>
+template <typename T, int N, int MODE, int BCT = -1, bool RAT = false, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) col2_kernel(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    col2_body<T, N, MODE, BCT, RAT>(a, blockIdx.x, blockIdx.y, smem_raw);
+    col2_body<T, N, MODE, BCT, RAT, PAIR>(a, blockIdx.x, blockIdx.y, smem_raw, blockIdx.z);
 }
 
 template <typename T, int N, int MODE, int BCT = -1>
@@ -425,6 +506,15 @@ cudaError_t col2_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_
     const size_t smem = TileOf<T, N>::E::smem_bytes();
     void (*k)(const ColArgs<T>) = nullptr;
     if constexpr (sizeof(T) == 4) {
+        if (!a.CL && a.cstride == 2 && a.in_sp > 0) {   // slow-axis passes on element pairs
+            switch (mode) {
+                case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, false, true>; break;
+                case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, false, true>; break;
+                case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, false, true>; break;
+                case MODE_TD: k = col2_kernel<T, N, MODE_TD, BCT, false, true>; break;
+                default: break;
+            }
+        }
         if (a.CL) {   // rational-coefficient mode
             switch (mode) {
                 case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, true>; break;
@@ -473,7 +563,11 @@ cudaError_t prepare2_bc() {
     }
     if constexpr (sizeof(T) == 4) {
         void (*kr[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_TA, BCT, true>, col2_kernel<T, N, MODE_TB, BCT, true>,
-                                          col2_kernel<T, N, MODE_TC, BCT, true>, col2_kernel<T, N, MODE_TD, BCT, true>};
+                                          col2_kernel<T, N, MODE_TC, BCT, true>, col2_kernel<T, N, MODE_TD, BCT, true>,
+                                          col2_kernel<T, N, MODE_TA, BCT, false, true>,
+                                          col2_kernel<T, N, MODE_TB, BCT, false, true>,
+                                          col2_kernel<T, N, MODE_TC, BCT, false, true>,
+                                          col2_kernel<T, N, MODE_TD, BCT, false, true>};
         for (auto k : kr) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -103,6 +103,7 @@ struct ColArgs {
     long long clB;
     int cstride;          // x distance between the tile columns of neighbouring lanes (2: lines A and B
                           // are the adjacent columns x, x + 1 of one array, read and written as pairs)
+    long long in_sp, out_sp;   // species stride (elements) of blockIdx.z; 0 when species are tile lines
 };
 
 template <typename T>
