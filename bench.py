@@ -192,6 +192,7 @@ def main():
     import torch
     import torch.distributed as dist
     import paper_2003_13569_gb300 as sf
+    from paper_2003_13569_gb300.shard import instance_dof, max_over_ranks, shard_instances
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -227,10 +228,7 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop() if clocks else None
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     value = dof * args.steps * world / (ms * 1e-3)
 
     # per-launch profile of the same step (events on the launching stream)
@@ -315,25 +313,33 @@ def main():
             del sr
             torch.cuda.empty_cache()
 
-    # the batched workload: 256 Gierer-Meinhardt instances, one persistent launch per pass
-    if rank == 0 and args.batched_steps > 0:
-        cfgs = W.gm_instances(256, seed=3)
+    # the batched workload: 256 Gierer-Meinhardt instances, one persistent launch per pass; with several
+    # ranks each takes whole instances (no data-path collective) and the slowest rank sets the time
+    if args.batched_steps > 0:
+        cfgs_all = W.gm_instances(256, seed=3)
+        mine = shard_instances(cfgs_all, world, rank)
+        cfgs = [cfgs_all[i] for i in mine]
         bt = sf.Batch(cfgs, dtype="f32")
         sched = bt.autotune(steps=2)          # blocks per SM and radix order (shared-memory engine sides)
         bt.load([np.stack(W.initial_fields(c)) for c in cfgs])
         bt.advance(3)
         torch.cuda.synchronize()
+        barrier()
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
         b0.record(bt.stream)
         bt.advance(args.batched_steps)
         b1.record(bt.stream)
         torch.cuda.synchronize()
-        msb = b0.elapsed_time(b1)
-        sides = sorted(set(int(c["N"][0]) for c in cfgs))
-        extra["batched"] = {"value": bt.dof * args.batched_steps / (msb * 1e-3), "unit": "DOF-steps/s",
+        barrier()
+        msb = max_over_ranks(b0.elapsed_time(b1))
+        sides = sorted(set(int(c["N"][0]) for c in cfgs_all))
+        dof_all = sum(instance_dof(c) for c in cfgs_all)
+        extra["batched"] = {"value": dof_all * args.batched_steps / (msb * 1e-3), "unit": "DOF-steps/s",
                             "ms_per_step": msb / args.batched_steps, "steps": args.batched_steps,
-                            "instances": bt.count, "dof": bt.dof, "launches_per_step": bt.launches_per_step,
+                            "instances": len(cfgs_all), "dof": dof_all, "instances_per_rank": len(mine),
+                            "placement": "whole instances per rank, longest first (no collective)",
+                            "launches_per_step": bt.launches_per_step,
                             "schedule": {"blocks_per_sm": sched[0], "radix_order_rule": sched[1],
                                          "chosen_by": "sfrd_batch_autotune (2 timed steps per candidate)"},
                             "workload": "2D fractional Gierer-Meinhardt, 256 instances, sides %s, BC P/D/N and "
@@ -353,10 +359,7 @@ def main():
         solver.run_host_ptr(host_in.data_ptr(), host_out.data_ptr(), 0.0, args.steps)
     el = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(el)
     fbytes = host_in.numel() * host_in.element_size()
     e2e = {"value": dof * args.steps * ncalls * world / el, "unit": "DOF-steps/s",
            "h2d_bytes_per_step": fbytes / args.steps, "d2h_bytes_per_step": fbytes / args.steps,
