@@ -495,11 +495,11 @@ static Arr<T> dense_arr(const Plan& p, const void* ptr) {
 }
 
 // pair_grid: for a slow-axis pass of an FP32 two-species plan on the register engine with internal
-// arrays and stored coefficients, the lines A and B are the adjacent columns x, x + 1 of one species
-// and the species is blockIdx.z (the slow-axis kernels then read and write element pairs).
+// arrays, the lines A and B are the adjacent columns x, x + 1 of one species and the species is
+// blockIdx.z (the slow-axis kernels then read and write element pairs).
 template <typename T>
 static bool use_pair_grid(const Plan& p, int d, const Arr<T>& in, const Arr<T>& out) {
-    return sizeof(T) == 4 && p.S == 2 && p.v2[d] && p.coef_mode == SFRD_COEF_STORED && d == (p.dim == 3 ? 2 : 1) &&
+    return sizeof(T) == 4 && p.S == 2 && p.v2[d] && d == (p.dim == 3 ? 2 : 1) &&
            in.pitch % 4 == 0 && out.pitch % 4 == 0 && in.xlim == in.pitch && out.xlim == out.pitch;
 }
 
@@ -575,6 +575,7 @@ static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>&
         a.CL = wsT<T>(p, p.off_CL);
         for (int h = 0; h < 2; ++h) a.cl_mult[h] = p.cl_shared ? p.kappa[h] : 1.0;
         a.clB = p.cl_shared ? 0 : a.in_offB;
+        a.cl_sp = p.cl_shared ? 0 : p.plane;
     }
     a.clock = reinterpret_cast<Clock*>(p.ws + p.off_clock);
     a.ax = axis_dev<T>(p, d);

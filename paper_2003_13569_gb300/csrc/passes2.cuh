@@ -41,7 +41,7 @@ __device__ __forceinline__ int unknowns(int n_runtime) {
 // RAT: the combination evaluates the coefficients from L (rational-coefficient mode).
 // PAIR (FP32 slow-axis stage passes): lines A and B are the adjacent columns x, x + 1 of the species
 // bz (ColArgs::cstride == 2, internal arrays), so every element access of the combination is one
-// 8-byte pair (16 bytes for the coefficient pairs, 2 x 16 for the quads).
+// 8-byte pair (16 bytes for the coefficient pairs, 2 x 16 for the quads; 8 bytes of L with RAT).
 template <typename T, int N, int MODE, int BCT = -1, bool RAT = false, bool PAIR = false>
 __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, unsigned char* smem_raw, int bz = 0) {
     constexpr int CC = TileOf<T, N>::CC;
@@ -198,6 +198,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         T ld[2 * B][2][NV];
         const bool ok[2] = {okA, okB};
         const unsigned clB = (unsigned)a.clB;
+        const unsigned clsub = PAIR && RAT ? (unsigned)((long long)bz * (a.in_sp - a.cl_sp)) : 0u;
         auto pre = [&](int slot, int k) {
             const unsigned eA = e0 + (unsigned)k * s_in;
 #pragma unroll
@@ -208,7 +209,27 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                 // before its own update); coefficient pairs and quads as single vector loads
                 if constexpr (PAIR) {
                     if (h || !ok[0]) continue;   // both lines at once
-                    if (MODE == MODE_TA || MODE == MODE_TB || MODE == MODE_TC) {
+                    if constexpr (RAT) {
+                        const float2 l = __ldg(reinterpret_cast<const float2*>(a.CL + (eA - clsub)));
+                        const float2 u = __ldg(reinterpret_cast<const float2*>(a.U + eA));
+                        if (MODE == MODE_TD) {
+                            const float2 f1 = __ldg(reinterpret_cast<const float2*>(a.F1 + eA));
+                            const float2 f2 = __ldg(reinterpret_cast<const float2*>(a.F2 + eA));
+                            const float2 f3 = __ldg(reinterpret_cast<const float2*>(a.F3 + eA));
+                            ld[slot][0][4] = l.x; ld[slot][1][4] = l.y;
+                            ld[slot][0][0] = u.x; ld[slot][1][0] = u.y;
+                            ld[slot][0][1] = f1.x; ld[slot][1][1] = f1.y;
+                            ld[slot][0][2] = f2.x; ld[slot][1][2] = f2.y;
+                            ld[slot][0][3] = f3.x; ld[slot][1][3] = f3.y;
+                        } else if (MODE != MODE_T0) {
+                            ld[slot][0][0] = l.x; ld[slot][1][0] = l.y;
+                            ld[slot][0][2] = u.x; ld[slot][1][2] = u.y;
+                            if (MODE == MODE_TC) {
+                                const float2 f1 = __ldg(reinterpret_cast<const float2*>(a.F1 + eA));
+                                ld[slot][0][3] = f1.x; ld[slot][1][3] = f1.y;
+                            }
+                        }
+                    } else if (MODE == MODE_TA || MODE == MODE_TB || MODE == MODE_TC) {
                         const float4 q = __ldg(reinterpret_cast<const float4*>(a.CQ + 2 * (size_t)eA));
                         const float2 u = __ldg(reinterpret_cast<const float2*>(a.U + eA));
                         ld[slot][0][0] = q.x; ld[slot][0][1] = q.y; ld[slot][1][0] = q.z; ld[slot][1][1] = q.w;
@@ -275,6 +296,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         };
         T* const F4 = a.F4;
         const T lm[2] = {(T)a.cl_mult[0], (T)a.cl_mult[1]};
+        const T lmz = (T)a.cl_mult[bz & 1];   // element-pair grid: both lines are species bz
         const T tau = (T)a.tau;
         E::post_b<B>(buf, red, red2, bc, c, g, pre, [&](int slot, int k, C Fv) {
             const unsigned eA = e0 + (unsigned)k * s_in;
@@ -284,7 +306,14 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
                 T sv[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const T* L = ld[slot][h];
+                    T Lc[NV];
+#pragma unroll
+                    for (int m = 0; m < NV; ++m) Lc[m] = ld[slot][h][m];
+                    if (RAT) {
+                        if (MODE == MODE_TD) p13_rphi<T>(lmz * Lc[4], tau, Lc[4], Lc[5], Lc[6], Lc[7]);
+                        else if (MODE != MODE_T0) p13_qphi<T>(lmz * Lc[0], tau, Lc[0], Lc[1]);
+                    }
+                    const T* L = Lc;
                     if (MODE == MODE_TA || MODE == MODE_TB) {
                         sv[h] = L[0] * L[2] + L[1] * F[h];
                     } else if (MODE == MODE_TC) {
@@ -506,16 +535,25 @@ cudaError_t col2_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_
     const size_t smem = TileOf<T, N>::E::smem_bytes();
     void (*k)(const ColArgs<T>) = nullptr;
     if constexpr (sizeof(T) == 4) {
-        if (!a.CL && a.cstride == 2 && a.in_sp > 0) {   // slow-axis passes on element pairs
-            switch (mode) {
-                case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, false, true>; break;
-                case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, false, true>; break;
-                case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, false, true>; break;
-                case MODE_TD: k = col2_kernel<T, N, MODE_TD, BCT, false, true>; break;
-                default: break;
+        if (a.cstride == 2 && a.in_sp > 0) {   // slow-axis passes on element pairs
+            if (a.CL) {
+                switch (mode) {
+                    case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, true, true>; break;
+                    case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, true, true>; break;
+                    case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, true, true>; break;
+                    case MODE_TD: k = col2_kernel<T, N, MODE_TD, BCT, true, true>; break;
+                    default: break;
+                }
+            } else {
+                switch (mode) {
+                    case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, false, true>; break;
+                    case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, false, true>; break;
+                    case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, false, true>; break;
+                    case MODE_TD: k = col2_kernel<T, N, MODE_TD, BCT, false, true>; break;
+                    default: break;
+                }
             }
-        }
-        if (a.CL) {   // rational-coefficient mode
+        } else if (a.CL) {   // rational-coefficient mode
             switch (mode) {
                 case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, true>; break;
                 case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, true>; break;
@@ -567,7 +605,11 @@ cudaError_t prepare2_bc() {
                                           col2_kernel<T, N, MODE_TA, BCT, false, true>,
                                           col2_kernel<T, N, MODE_TB, BCT, false, true>,
                                           col2_kernel<T, N, MODE_TC, BCT, false, true>,
-                                          col2_kernel<T, N, MODE_TD, BCT, false, true>};
+                                          col2_kernel<T, N, MODE_TD, BCT, false, true>,
+                                          col2_kernel<T, N, MODE_TA, BCT, true, true>,
+                                          col2_kernel<T, N, MODE_TB, BCT, true, true>,
+                                          col2_kernel<T, N, MODE_TC, BCT, true, true>,
+                                          col2_kernel<T, N, MODE_TD, BCT, true, true>};
         for (auto k : kr) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -97,10 +97,13 @@ struct ColArgs {
     int S;
     double alpha[2], kappa[2], tau;
     // SFRD_COEF_RATIONAL: the slow-axis combinations evaluate the coefficients from L = cl_mult[h] *
-    // CL[i + (h ? clB : 0)] (line h of the tile); CL == nullptr with stored coefficient arrays
+    // CL[i + (h ? clB : 0)] (line h of the tile); CL == nullptr with stored coefficient arrays.  On the
+    // element-pair grid (species s = blockIdx.z, both lines of species s) the L of element i of species
+    // s is cl_mult[s] * CL[i - s * (in_sp - cl_sp)]: cl_sp is the species stride of CL (0 when the
+    // species share one plane of tau Lambda^{alpha/2}).
     const T* CL;
     double cl_mult[2];
-    long long clB;
+    long long clB, cl_sp;
     int cstride;          // x distance between the tile columns of neighbouring lanes (2: lines A and B
                           // are the adjacent columns x, x + 1 of one array, read and written as pairs)
     long long in_sp, out_sp;   // species stride (elements) of blockIdx.z; 0 when species are tile lines
