@@ -336,11 +336,32 @@ struct Eng {
             const C zh = buf[H * LD + c];     // k = N/2: R = Re, I = 0 for both lines
             nyq = zh;
         }
-        if (bc != SFRD_BC_PERIODIC) red[g * CC + c] = run;
-        __syncthreads();   // all reads of Z done: the buffer becomes V
+        // running sums of the groups before this one (same column): within the warp by an exclusive
+        // shuffle scan over its 32 / CC groups, across warps from the per-warp column totals in red
+        static_assert(32 % CC == 0, "a warp holds whole groups");
+        constexpr int GPW = 32 / CC;           // groups per warp
+        const int w = g / GPW, lane = (g % GPW) * CC + c;
         C pre_sum = czero<C>();
         if (bc != SFRD_BC_PERIODIC) {
-            for (int q = 0; q < g; ++q) pre_sum = cadd(pre_sum, red[q * CC + c]);
+            if (GPW > 1) {
+                C ex;                          // the shifted sequence: running sum of the previous group
+                ex.x = __shfl_up_sync(0xffffffffu, run.x, CC);
+                ex.y = __shfl_up_sync(0xffffffffu, run.y, CC);
+                if (lane < CC) ex = czero<C>();
+#pragma unroll
+                for (int d = CC; d < 32 - CC; d *= 2) {
+                    C t;
+                    t.x = __shfl_up_sync(0xffffffffu, ex.x, d);
+                    t.y = __shfl_up_sync(0xffffffffu, ex.y, d);
+                    if (lane >= d) ex = cadd(ex, t);
+                }
+                pre_sum = ex;
+            }
+            if (lane >= 32 - CC) red[w * CC + c] = cadd(pre_sum, run);
+        }
+        __syncthreads();   // all reads of Z done: the buffer becomes V
+        if (bc != SFRD_BC_PERIODIC) {
+            for (int q = 0; q < w; ++q) pre_sum = cadd(pre_sum, red[q * CC + c]);
         }
         // output q (0, 1) of pair t: index and value, or false when there is none
         auto out_of = [&](int t, int q, int& i, C& v) -> bool {
