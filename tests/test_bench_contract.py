@@ -1,0 +1,68 @@
+"""The benchmark's command-line contract on the CPU: the reference arm (the FP64 oracle on a bounded sample)
+prints one JSON line with the required keys on rank 0 and nothing on other ranks, and the product arm and the
+package refuse to run without the CUDA library and a GPU instead of falling back to anything."""
+import json
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BENCH = os.path.join(ROOT, "bench.py")
+
+
+def _run(args, env_extra=None, timeout=300):
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, BENCH] + args, capture_output=True, text=True, env=env, timeout=timeout,
+                          cwd=ROOT)
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = _run(["--impl", "reference", "--steps", "2", "--warmup", "1"], {"SFRD_REF_N": "8"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["unit"] == "DOF-steps/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["data"] == "synthetic" and d["dtype"] == "f64" and d["vs_baseline"] is None
+    assert "255^3" in d["config"]["workload"] and d["config"]["sample_grid"] == [8, 8, 8]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "N=8" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_prints_nothing_on_other_ranks():
+    r = _run(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"SFRD_REF_N": "8", "RANK": "1"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
+
+
+def test_product_arm_without_a_gpu_fails_without_a_result_line():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the product arm would run")
+    r = _run(["--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--fp64-steps", "0", "--batched-steps", "0",
+              "--rational-steps", "0"])
+    assert r.returncode != 0
+    assert not any(ln.lstrip().startswith("{") for ln in r.stdout.splitlines())
+
+
+def test_package_refuses_to_import_without_the_library(tmp_path):
+    pkg = tmp_path / "sfrd_copy"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2003_13569_gb300", "__init__.py"), pkg / "__init__.py")
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "try:\n    import sfrd_copy\nexcept ImportError as e:\n    print('refused:', e)\n    sys.exit(0)\n"
+            "sys.exit(1)\n" % str(tmp_path))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "libsfrd.so is not built" in r.stdout
