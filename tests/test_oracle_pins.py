@@ -249,6 +249,47 @@ def test_single_eigenmode_decays_by_r13_power():
         np.testing.assert_allclose(got, expect, atol=1e-12 * np.abs(expect).max())
 
 
+def _closed_form_lambda(bc, n, N, h):
+    """The compact scheme's eigenvalue of mode n on N intervals (Section 3.1; periodic angle by reading R1)."""
+    s = math.sin(n * math.pi / N) ** 2 if bc == O.PERIODIC else math.sin(n * math.pi / (2 * N)) ** 2
+    return 4.0 * s / (h * h * (1.0 - s / 3.0))
+
+
+def _closed_form_mode(bc, n, N):
+    """The grid function of mode n at the unknowns: cos(2 pi n i / N), i < N (periodic); sin(n pi i / N),
+    0 < i < N (Dirichlet); cos(n pi i / N), 0 <= i <= N (Neumann)."""
+    if bc == O.PERIODIC:
+        return np.cos(2 * np.pi * n * np.arange(N) / N)
+    if bc == O.DIRICHLET:
+        return np.sin(np.pi * n * np.arange(1, N) / N)
+    return np.cos(np.pi * n * np.arange(N + 1) / N)
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+def test_separable_3d_eigenmodes_decay_by_closed_form_r13(bc):
+    """f = 0 on a 3D grid with different sides: a product of 1D modes is an eigenvector of the summed operator
+    with eigenvalue lambda_x + lambda_y + lambda_z (closed forms of Section 3), so after M steps it is scaled
+    by R13(L)^M with L = kappa tau (lambda_x + lambda_y + lambda_z)^{alpha/2} (Eqs. E22 and ETDRK4P13),
+    R13(L) = (24 - 6L) / (24 + 18L + 6L^2 + L^3).  The expected field uses none of the oracle's tables."""
+    Ns, lo, hi = (8, 10, 6), (0.0, -1.0, 0.5), (1.0, 1.5, 2.0)
+    alpha, kappa, tau, M = 1.6, 0.7, 0.05, 5
+    g = O.Grid(Ns, lo, hi)
+    f, J = O.linear(0.0)
+    s = O.ETDRK4P13(O.Problem(g, bc, [alpha], [kappa], tau, f, dreaction=J, nspecies=1))
+    U0 = np.zeros(g.shape(bc))
+    expect = np.zeros_like(U0)
+    for (nx, ny, nz), wgt in (((1, 2, 3), 1.0), ((3, 1, 2), -0.6), ((2, 4, 1), 0.3)):
+        modes = [_closed_form_mode(bc, n, N) for n, N in zip((nx, ny, nz), Ns)]
+        F = wgt * np.einsum("z,y,x->zyx", modes[2], modes[1], modes[0])
+        lam = sum(_closed_form_lambda(bc, n, N, (b - a) / N) for n, N, a, b in zip((nx, ny, nz), Ns, lo, hi))
+        L = kappa * tau * lam ** (alpha / 2)
+        R = (24 - 6 * L) / (24 + 18 * L + 6 * L * L + L ** 3)
+        U0 += F
+        expect += R ** M * F
+    got = s.run([U0], 0.0, M)[0]
+    np.testing.assert_allclose(got, expect, atol=1e-12 * np.abs(U0).max())
+
+
 @pytest.mark.parametrize("bc", [O.PERIODIC, O.NEUMANN])
 def test_zero_mode_is_conserved_without_reaction(bc):
     N = 12
