@@ -16,6 +16,7 @@ weak scaling.  --impl reference times the FP64 CPU oracle on the host cores.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -39,7 +40,7 @@ WORKLOAD = "schnak256"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
@@ -67,14 +68,42 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def summarise_clocks(rows, t0=None, t1=None):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in nvidia-smi rows
+    (timestamp, index, clocks.sm, clocks.max.sm, power.draw, reasons.active, hw_slowdown,
+    hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap), keeping the samples taken inside the
+    wall-clock interval [t0, t1] (all samples when none fall inside or no interval is given)."""
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    parsed = []
+    for r in rows:
+        try:
+            vals = (float(r[2]), float(r[3]),
+                    [nm for i, nm in enumerate(names) if r[6 + i].strip().lower() == "active"])
+        except (ValueError, IndexError):
+            continue
+        try:
+            ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        parsed.append((ts,) + vals)
+    inside = [p for p in parsed if None not in (p[0], t0, t1) and t0 <= p[0] <= t1]
+    use = inside if inside else parsed
+    sm = [p[1] for p in use]
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(p[2] for p in use) if use else None,
+            "reasons": sorted(set(nm for p in use for nm in p[3])), "samples": len(use),
+            "samples_in_timed_region": len(inside)}
+
+
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling (every 200 ms) around the timed region; the summary keeps the samples
+    taken between mark() and stop()."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
+        self.t0 = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
@@ -83,9 +112,15 @@ class Clocks:
         except Exception:
             self.p = None
 
+    def mark(self):
+        """Start of the timed region (wall clock)."""
+        self.t0 = time.time()
+
     def stop(self):
+        t1 = time.time()
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)   # the sample that covers the end of the region
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -94,19 +129,7 @@ class Clocks:
         self.f.flush()
         rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
         os.unlink(self.f.name)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            try:
-                sm.append(float(r[1]))
-                mx.append(float(r[2]))
-                for i, nm in enumerate(names):
-                    if r[5 + i].strip().lower() == "active":
-                        reasons.add(nm)
-            except (ValueError, IndexError):
-                continue
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarise_clocks(rows, self.t0, t1)
 
 
 # Algorithmic HBM words per unknown (per species element) of each pass kind (fixed pass model).
@@ -219,6 +242,8 @@ def main():
     time.sleep(0.3 if clocks else 0.0)
     barrier()
     torch.cuda.synchronize()
+    if clocks:
+        clocks.mark()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)

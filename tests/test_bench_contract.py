@@ -66,3 +66,27 @@ def test_package_refuses_to_import_without_the_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "libsfrd.so is not built" in r.stdout
+
+
+def test_clock_summary_keeps_the_samples_of_the_timed_region():
+    import datetime
+    sys.path.insert(0, ROOT)
+    import bench
+    t = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def row(dt, sm, hw="Not Active", cap="Not Active"):
+        ts = (t + datetime.timedelta(seconds=dt)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return [ts, "0", str(sm), "2070", "900.5", "0x0", hw, "Not Active", "Not Active", cap]
+
+    rows = [row(0.0, 1400), row(0.2, 2070), row(0.4, 2055, cap="Active"), row(0.6, 2070), row(0.8, 1500,
+                                                                                              hw="Active")]
+    t0, t1 = (t + datetime.timedelta(seconds=0.1)).timestamp(), (t + datetime.timedelta(seconds=0.7)).timestamp()
+    c = bench.summarise_clocks(rows, t0, t1)
+    assert c["samples_in_timed_region"] == 3 and c["samples"] == 3
+    assert c["sm_mhz"] == 2070 and c["sm_max_mhz"] == 2070
+    assert c["reasons"] == ["sw_power_cap"]                 # the hw_slowdown sample lies after the region
+    c = bench.summarise_clocks(rows)                         # no interval: every sample
+    assert c["samples"] == 5 and c["samples_in_timed_region"] == 0
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"] and c["sm_mhz"] == 2055
+    bad = [["not a time"] + r[1:] for r in rows]             # unparsable timestamps: every sample, none dropped
+    assert bench.summarise_clocks(bad, t0, t1)["samples"] == 5
