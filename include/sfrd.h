@@ -1,10 +1,12 @@
 /*
  * sfrd.h -- C ABI of the GB300 (sm_103a) compact-MTT ETDRK4-P13 solver for
- * space-fractional reaction-diffusion equations (Bhatt et al., arXiv 2003.13569).
+ * space-fractional reaction-diffusion equations (arXiv 2003.13569, "Fast and
+ * accurate high-order method for high dimensional space-fractional
+ * reaction-diffusion equation with general boundary conditions").
  *
  * Problem (Section 1, Eq. 1):
  *     du_s/dt = -kappa_s (-Delta)^{alpha_s/2} u_s + f_s(u, t),   1 < alpha_s <= 2,
- * on a box in R^d (d = 2, 3) with periodic, homogeneous Dirichlet or homogeneous
+ * on a box in R^d (d = 1, 2, 3) with periodic, homogeneous Dirichlet or homogeneous
  * Neumann boundary conditions, one to two species s.
  *
  * Space (Section 3): the fractional Laplacian is the matrix transfer technique
@@ -22,7 +24,7 @@
  *     Unknowns per axis: N (periodic: nodes 0..N-1), N-1 (Dirichlet: nodes
  *     1..N-1), N+1 (Neumann: nodes 0..N).
  *   - Field layout (device or host, as each call says): species-major, dense,
- *     row-major [S][n_z][n_y][n_x] (3D) or [S][n_y][n_x] (2D), x fastest, in
+ *     row-major [S][n_z][n_y][n_x] (3D), [S][n_y][n_x] (2D) or [S][n_x] (1D), x fastest, in
  *     the plan's dtype (double for SFRD_F64, float for SFRD_F32).
  *   - Ownership: the caller owns every field buffer, the workspace and the
  *     stream; the plan owns only host metadata and its CUDA graph.  Device

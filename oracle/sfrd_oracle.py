@@ -1,5 +1,6 @@
 """Plain FP64 CPU oracle for the compact-MTT ETDRK4-P13 solver of space-fractional
-reaction-diffusion equations (Bhatt et al., arXiv 2003.13569).
+reaction-diffusion equations (arXiv 2003.13569, "Fast and accurate high-order method for high dimensional
+space-fractional reaction-diffusion equation with general boundary conditions").
 
 TEST INFRASTRUCTURE ONLY.  tests/, __graft_entry__.smoke() and bench.py's CPU
 baseline / reference arm are the only code allowed to import this module.  The
@@ -37,8 +38,13 @@ Readings where the paper is garbled or silent (each pinned by a CPU test):
       forward map (grid values -> eigen-coefficients) is C^{-1} = (2/N) W C W,
       W = diag(1/2, 1, ..., 1, 1/2);
   R5  c-stage uses a^k (Eq. ETDRK4P13 and Algorithm 1);
-  R6  Example 1 source term carries a single kappa; Table 1 uses kappa = 10, T = 1;
-  R7  Example 2: the third term of Phi is (40 pi^2)^{alpha/2}.
+  R8  Example 1's source term carries a single kappa;
+  R9  Table 1 uses kappa = 10, T = 1 and tau = h / (4 kappa);
+  R10 Example 2: the third term of Phi is (40 pi^2)^{alpha/2};
+  R12 a zero eigenvalue (L = 0) needs no special case: the rationals take their limits there;
+  R16 the reaction is evaluated at t_k, t_k + tau/2, t_k + tau/2, t_k + tau in the four stages;
+  R17 the Cox-Matthews variant puts e^{-L}, e^{-L/2} and the exponential phi-functions in the
+      places of the Pade-(1,3) rationals.
 """
 
 from __future__ import annotations
@@ -616,7 +622,7 @@ def linear(gamma: float) -> tuple:
 
 def fisher_mms(grid: Grid, kappa: float, alpha: float):
     """Example 1: f(u,t) = -2e^{-t}s^3 + (kappa/4)e^{-t}(3(2pi)^a sin 2pi x - (6pi)^a sin 6pi x)
-    + e^{-2t}s^6 + u - u^2, s = sin(2 pi x)  (reading R6: a single kappa)."""
+    + e^{-2t}s^6 + u - u^2, s = sin(2 pi x)  (reading R8: a single kappa)."""
     x = grid.mesh(DIRICHLET)[0]
     s = np.sin(2 * np.pi * x)
     src = (kappa / 4.0) * (3 * (2 * np.pi) ** alpha * np.sin(2 * np.pi * x)
@@ -633,7 +639,7 @@ def fisher_mms(grid: Grid, kappa: float, alpha: float):
 
 
 def huxley_mms(grid: Grid, bc: str, kappa: float, alpha: float):
-    """Example 2: u(1-u)(u-1) + source with exact u = t^alpha cos^3(2pi x) cos^3(2pi y) (reading R7)."""
+    """Example 2: u(1-u)(u-1) + source with exact u = t^alpha cos^3(2pi x) cos^3(2pi y) (reading R10)."""
     X, Y = grid.mesh(bc)
     g = np.cos(2 * np.pi * X) ** 3 * np.cos(2 * np.pi * Y) ** 3
     c = np.cos
