@@ -49,7 +49,7 @@ extern "C" {
 /* ---- error codes ------------------------------------------------------- */
 #define SFRD_OK            0
 #define SFRD_EINVAL       -1  /* bad argument: alpha not in (1,2], kappa < 0, dt <= 0, N < 2, ... */
-#define SFRD_EUNSUPPORTED -2  /* valid problem outside what this build handles (length not
+#define SFRD_EUNSUPPORTED -2  /* valid problem outside what the library handles (length not
                                  {2,3,5}-smooth, FFT length > 1024, a field
                                  array of 2^32 elements or more, ...) */
 #define SFRD_ENOWS        -3  /* workspace missing, too small or not bound */
