@@ -353,6 +353,104 @@ def test_table_orders_are_four():
 
 
 # --------------------------------------------------------------------------
+# Section 5.2: reaction terms, pinned by properties of the printed models (conserved combinations,
+# homogeneous steady states, nullclines, degrees of homogeneity) rather than by their formulas
+# --------------------------------------------------------------------------
+
+def _grid_uv(lo=0.2, hi=2.0, n=7):
+    u, v = np.meshgrid(np.linspace(lo, hi, n), np.linspace(lo + 0.1, hi + 0.3, n), indexing="ij")
+    return u.ravel(), v.ravel()
+
+
+def test_fitzhugh_nagumo_cubic_nullcline_and_affine_recovery():
+    mu, eps, beta, gamma, delta = 0.13, 0.02, 0.7, 1.3, 0.05
+    f, _, _ = O.fitzhugh_nagumo(mu=mu, eps=eps, beta=beta, gamma=gamma, delta=delta)
+    u = np.linspace(-1.0, 2.0, 9)
+    fu0 = f([u, np.zeros_like(u)], 0.0)[0]
+    c = np.polyfit(u, fu0, 3)                     # f_u(u, 0): a cubic with leading coefficient -1
+    assert abs(c[0] + 1.0) < 1e-12
+    np.testing.assert_allclose(np.sort(np.roots(c).real), [0.0, mu, 1.0], atol=1e-10)
+    for v in (-0.4, 0.9):                         # f_u depends on v only through -v
+        np.testing.assert_allclose(f([u, np.full_like(u, v)], 0.0)[0], fu0 - v, atol=1e-14)
+    # f_v is affine with gradient eps (beta, -gamma) and vanishes on the line beta u - gamma v = delta
+    uu = np.array([0.0, 1.0, -2.0])
+    vv = (beta * uu - delta) / gamma
+    np.testing.assert_allclose(f([uu, vv], 0.0)[1], 0.0, atol=1e-15)
+    np.testing.assert_allclose(f([uu + 1, vv], 0.0)[1], eps * beta, rtol=1e-12)
+    np.testing.assert_allclose(f([uu, vv + 1], 0.0)[1], -eps * gamma, rtol=1e-12)
+
+
+def test_gray_scott_exchange_cancels_and_cubic_term():
+    F, K = 0.037, 0.06
+    f, _ = O.gray_scott(F, K)
+    u, v = _grid_uv()
+    fu, fv = f([u, v], 0.0)
+    # the autocatalytic u v^2 moves mass from u to v: the sum is linear
+    np.testing.assert_allclose(fu + fv, F * (1 - u) - (F + K) * v, atol=1e-14)
+    g = lambda a, b: f([a, b], 0.0)[0] - F * (1 - a)          # the nonlinear part of f_u
+    np.testing.assert_allclose(g(2 * u, v), 2 * g(u, v), atol=1e-13)   # degree 1 in u
+    np.testing.assert_allclose(g(u, 2 * v), 4 * g(u, v), atol=1e-13)   # degree 2 in v
+    assert abs(g(np.array(1.0), np.array(1.0)) + 1.0) < 1e-15          # coefficient -1
+    assert np.all(np.asarray(f([u, 0 * v], 0.0)[1]) == 0)              # no v, no source of v
+
+
+def test_schnakenberg_steady_state_and_exchange():
+    gam, a, b = 1000.0, 0.1, 0.9
+    f, _ = O.schnakenberg(gamma=gam, a=a, b=b)
+    Us, Vs = a + b, b / (a + b) ** 2                                  # the homogeneous steady state
+    r = f([np.array([Us]), np.array([Vs])], 0.0)
+    assert max(abs(r[0][0]), abs(r[1][0])) < 1e-12
+    u, v = _grid_uv()
+    fu, fv = f([u, v], 0.0)
+    np.testing.assert_allclose(fu + fv, gam * (a + b - u), rtol=1e-13, atol=1e-10)
+    h = lambda p, q: f([p, q], 0.0)[1] - gam * b                        # the nonlinear part of f_v
+    np.testing.assert_allclose(h(2 * u, v), 4 * h(u, v), rtol=1e-13)   # degree 2 in u
+    np.testing.assert_allclose(h(u, 2 * v), 2 * h(u, v), rtol=1e-13)   # degree 1 in v
+    # the perturbation form used with Dirichlet conditions: f evaluated at u* + w
+    fo, _ = O.schnakenberg(gamma=gam, a=a, b=b, ustar=(Us, Vs))
+    w = [u - Us, v - Vs]
+    for x, y in zip(fo(w, 0.0), (fu, fv)):
+        np.testing.assert_allclose(x, y, rtol=1e-12, atol=1e-9)
+
+
+def test_gierer_meinhardt_steady_state_nullcline_and_homogeneity():
+    c1, c2, c3, c4 = 1.0, 1.0, 1.0 / (0.04 * 0.1), 1.0 / 0.1          # the printed model: eps 0.04, mu 0.1
+    f, _ = O.gierer_meinhardt(c1, c2, c3, c4)
+    us = c1 * c4 / (c2 * c3)
+    vs = c3 * us * us / c4
+    r = f([np.array([us]), np.array([vs])], 0.0)
+    assert max(abs(r[0][0]), abs(r[1][0])) < 1e-12
+    u, v = _grid_uv()
+    fu, fv = f([u, v], 0.0)
+    np.testing.assert_allclose(f([2 * u, 2 * v], 0.0)[0], 2 * fu, rtol=1e-13)   # f_u homogeneous of degree 1
+    np.testing.assert_allclose(f([u, c1 * u / c2], 0.0)[0], 0.0, atol=1e-12)      # u-nullcline v = c1 u / c2
+    np.testing.assert_allclose(f([u, c3 * u * u / c4], 0.0)[1], 0.0, atol=1e-12)  # v-nullcline
+    np.testing.assert_allclose(f([u, v + 1.0], 0.0)[1] - fv, -c4, rtol=1e-12)     # f_v affine in v
+    # the unit model of the batched workload has the steady state (1, 1)
+    f1, _ = O.gierer_meinhardt()
+    assert max(abs(x[0]) for x in f1([np.array([1.0]), np.array([1.0])], 0.0)) == 0.0
+
+
+@pytest.mark.parametrize("name", ["fhn", "gray_scott", "schnakenberg", "gierer_meinhardt"])
+def test_reaction_jacobians_match_central_differences(name):
+    f, J = {"fhn": lambda: O.fitzhugh_nagumo()[:2], "gray_scott": O.gray_scott,
+            "schnakenberg": lambda: O.schnakenberg(ustar=(1.0, 0.9)), "gierer_meinhardt": O.gierer_meinhardt}[name]()
+    u, v = _grid_uv(0.3, 1.7, 5)
+    Jm = J([u, v], 0.0)
+    d = 1e-6
+    for s in range(2):
+        wp = [u.copy(), v.copy()]
+        wm = [u.copy(), v.copy()]
+        wp[s] += d
+        wm[s] -= d
+        fp, fm = f(wp, 0.0), f(wm, 0.0)
+        for r in range(2):
+            fd = (fp[r] - fm[r]) / (2 * d)
+            np.testing.assert_allclose(np.broadcast_to(Jm[r][s], fd.shape), fd,
+                                       rtol=1e-6, atol=1e-6 * max(1.0, np.abs(fd).max()))
+
+
+# --------------------------------------------------------------------------
 # Symmetry and the adjoint
 # --------------------------------------------------------------------------
 
