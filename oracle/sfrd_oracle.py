@@ -42,6 +42,9 @@ Readings where the paper is garbled or silent (each pinned by a CPU test):
   R9  Table 1 uses kappa = 10, T = 1 and tau = h / (4 kappa);
   R10 Example 2: the third term of Phi is (40 pi^2)^{alpha/2};
   R12 a zero eigenvalue (L = 0) needs no special case: the rationals take their limits there;
+  R14 Dirichlet conditions for Schnakenberg apply to the perturbation w about the homogeneous
+      steady state u* (the reaction is evaluated at u* + w): a modelling choice, parity unpinned
+      (the tests pin only that the perturbation form equals the reaction at u* + w);
   R16 the reaction is evaluated at t_k, t_k + tau/2, t_k + tau/2, t_k + tau in the four stages;
   R17 the Cox-Matthews variant puts e^{-L}, e^{-L/2} and the exponential phi-functions in the
       places of the Pade-(1,3) rationals.
