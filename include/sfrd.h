@@ -315,14 +315,41 @@ int sfrd_adjoint(sfrd_plan_t plan, double t0, int64_t nsteps, int64_t ckpt_every
  * Fields are passed as host arrays of count device pointers, field i laid out
  * [S][...] for instance i's grid.  Errors as for single plans. */
 typedef struct sfrd_batch_s* sfrd_batch_t;
+
+/* Host only.  grids, bcs: count entries; alpha, kappa: count * S entries
+ * (S = reaction->nspecies), all read during the call only.  Every instance is
+ * validated as by sfrd_plan; all share grids[0].dim, which must be 2 or 3
+ * (1D: SFRD_EUNSUPPORTED; an instance of another dim: SFRD_EINVAL), and have
+ * at most 512 intervals per axis (else SFRD_EUNSUPPORTED).  On success *out
+ * owns a new batch (release with sfrd_batch_destroy). */
 int sfrd_batch_plan(sfrd_batch_t* out, int64_t count, const sfrd_grid* grids, const int32_t* bcs,
                     const double* alpha, const double* kappa, double dt, int32_t dtype,
                     const sfrd_reaction* reaction);
+
+/* Bytes of device workspace for all instances (their states, stage spectra,
+ * coefficient arrays and tables) plus the work-item schedule. */
 int sfrd_batch_workspace_bytes(sfrd_batch_t batch, size_t* bytes);
+
+/* As sfrd_bind, for every instance at once: caller-owned workspace
+ * (>= sfrd_batch_workspace_bytes, 256-byte aligned) and a cudaStream_t.
+ * Errors: SFRD_ENOWS, SFRD_ECUDA. */
 int sfrd_batch_bind(sfrd_batch_t batch, void* workspace, size_t bytes, void* stream);
+
+/* u0: host array of count device pointers, u0[i] the physical field of
+ * instance i laid out [S][...] on its own grid (only read).  Transforms every
+ * instance to its resident spectral state and sets all clocks to t0. */
 int sfrd_batch_load(sfrd_batch_t batch, const void* const* u0, double t0);
+
+/* nsteps replays of the captured batched step (stream-ordered, no sync).
+ * Errors: SFRD_ESTATE before sfrd_batch_load, SFRD_ECUDA. */
 int sfrd_batch_advance(sfrd_batch_t batch, int64_t nsteps);
+
+/* u: host array of count device pointers; writes each instance's physical
+ * field (the resident state is kept). */
 int sfrd_batch_store(sfrd_batch_t batch, void* const* u);
+
+/* count, total unknowns over all instances and species, and kernel launches
+ * per batched step (a NULL output pointer is skipped). */
 int sfrd_batch_info(sfrd_batch_t batch, int64_t* count, int64_t* dof, int64_t* launches_per_step);
 /* Autotuner of the batched schedule: times `steps` batched steps for each
  * number of resident blocks per SM (1..4) of the persistent launches and each
