@@ -155,6 +155,19 @@ def ncu_traffic(kind_name):
     return None
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), for the baseline records."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(cfg, seconds):
     """The FP64 oracle (dense per-axis transforms, Algorithm 1) timed on the host cores."""
     from oracle.bridge import solver as oracle_solver
@@ -170,7 +183,8 @@ def cpu_baseline(cfg, seconds):
             break
     el = time.perf_counter() - t0
     dof = int(np.prod(W.field_shape(cfg))) * 2
-    return {"value": dof * n / el, "unit": "DOF-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": dof * n / el, "unit": "DOF-steps/s", "cores": os.cpu_count(), "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": "%d ETDRK4-P13 step(s) of the full %s workload, FP64 dense-matrix oracle, %.1f s"
                       % (n, "x".join(str(x) for x in W.field_shape(cfg)), el)}
 
@@ -200,7 +214,8 @@ def reference_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": workload_desc(W.config(WORKLOAD)),
                        "sample_grid": list(cfg["N"]), "parallelism": "replicas"},
-            "cpu_baseline": {"value": v, "unit": "DOF-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "DOF-steps/s", "cores": os.cpu_count(), "cpu_model": cpu_model(),
+                             "kind": "oracle",
                              "sample": "one FP64 oracle step per bench step on the same workload at N=%d "
                                        "(%d^3 interior)" % (Nsample, Nsample - 1)},
             "e2e": {"value": v, "unit": "DOF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -37,6 +37,7 @@ def test_reference_arm_prints_one_contract_line():
     assert "255^3" in d["config"]["workload"] and d["config"]["sample_grid"] == [8, 8, 8]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and "N=8" in d["cpu_baseline"]["sample"]
+    assert isinstance(d["cpu_baseline"]["cpu_model"], str) and d["cpu_baseline"]["cpu_model"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
