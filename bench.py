@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--fhn-steps", type=int, default=200,
+                    help="steps timed on the 2D FitzHugh-Nagumo workload, FP64 and FP32 (0: skip)")
     ap.add_argument("--rational-steps", type=int, default=50,
                     help="steps timed for the rational-coefficient variant (0: skip)")
     return ap.parse_args()
@@ -408,6 +410,32 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, args.cpu_seconds)
+
+    # the 2D FitzHugh-Nagumo workload (65^2 Neumann nodes, its 200 steps), FP64 and FP32: a small grid whose
+    # step is bound by launch latency rather than HBM; reported for completeness, errors kept in the record
+    if rank == 0 and args.fhn_steps > 0:
+        fcfg = W.config("fhn64")
+        extra["fhn64"] = {"workload": "2D fractional FitzHugh-Nagumo, Neumann (DCT-I), N=64 (65^2 nodes), "
+                                      "alpha=1.5, kappa=(1,0), dt=0.1", "steps": args.fhn_steps}
+        for dt in ("f64", "f32"):
+            try:
+                sfhn = sf.Solver(fcfg, dtype=dt)
+                sfhn.load(torch.as_tensor(np.stack(W.initial_fields(fcfg))), 0.0)
+                sfhn.advance(3)
+                torch.cuda.synchronize()
+                f0 = torch.cuda.Event(enable_timing=True)
+                f1 = torch.cuda.Event(enable_timing=True)
+                f0.record(sfhn.stream)
+                sfhn.advance(args.fhn_steps)
+                f1.record(sfhn.stream)
+                torch.cuda.synchronize()
+                msf = f0.elapsed_time(f1)
+                extra["fhn64"][dt] = {"value": sfhn.dof * args.fhn_steps / (msf * 1e-3), "unit": "DOF-steps/s",
+                                      "ms_per_step": msf / args.fhn_steps,
+                                      "gpu_launches_per_step": sfhn.kernels_per_step}
+                del sfhn
+            except Exception as exc:   # keep the headline line whatever happens here
+                extra["fhn64"][dt] = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DOF-steps/s", "n_gpus": world, "steps": args.steps,
