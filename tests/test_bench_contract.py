@@ -91,3 +91,22 @@ def test_clock_summary_keeps_the_samples_of_the_timed_region():
     assert c["reasons"] == ["hw_slowdown", "sw_power_cap"] and c["sm_mhz"] == 2055
     bad = [["not a time"] + r[1:] for r in rows]             # unparsable timestamps: every sample, none dropped
     assert bench.summarise_clocks(bad, t0, t1)["samples"] == 5
+
+
+def test_pass_model_and_committed_traffic():
+    sys.path.insert(0, ROOT)
+    import bench
+    launches_3d = {0: 4, 1: 8, 2: 1, 3: 1, 4: 1, 5: 1}       # x, middle, stages a-c, update
+    launches_2d = {0: 4, 2: 1, 3: 1, 4: 1, 5: 1}
+    assert sum(bench.WORDS[k] * n for k, n in launches_3d.items()) == 54
+    assert sum(bench.WORDS[k] * n for k, n in launches_2d.items()) == 38
+    dof = 2 * 255 ** 3
+    for kind, name in bench.KIND_NAME.items():
+        t = bench.ncu_traffic(name)
+        assert t is not None, name
+        # the captured DRAM bytes of a launch lie within [0.5, 1.2] x its algorithmic bytes (no re-reads;
+        # below 1 where the input was still in L2)
+        assert 0.5 < t / (bench.WORDS[kind] * dof * 4) < 1.2, (name, t)
+    assert bench.ncu_traffic("no_such_kernel") is None
+    peak, src = bench.peaks()
+    assert peak > 1000 and src in ("measured", "fallback")
