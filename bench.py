@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--adjoint-steps", type=int, default=500,
+                    help="steps of the timed checkpointed forward + adjoint run (0: skip)")
     ap.add_argument("--fhn-steps", type=int, default=200,
                     help="steps timed on the 2D FitzHugh-Nagumo workload, FP64 and FP32 (0: skip)")
     ap.add_argument("--rational-steps", type=int, default=50,
@@ -436,6 +438,36 @@ def main():
                 del sfhn
             except Exception as exc:   # keep the headline line whatever happens here
                 extra["fhn64"][dt] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+
+    # the discrete adjoint on its workload (2D FitzHugh-Nagumo, 257^2 Neumann nodes, FP64, checkpoints every
+    # 50 steps): one checkpointed forward run and one reverse sweep (with recomputation), timed by events
+    if rank == 0 and args.adjoint_steps > 0:
+        try:
+            acfg = W.config("fhn256_adjoint")
+            n, K = args.adjoint_steps, acfg["checkpoint_every"]
+            sa = sf.Solver(acfg, dtype="f64")
+            u0a = np.stack(W.initial_fields(acfg))
+            tgt = torch.as_tensor(np.stack(W.initial_fields(acfg, seed=acfg["target"]["seed"])),
+                                  device="cuda", dtype=torch.float64)
+            for timed in (False, True):            # the first pass allocates the checkpoint buffer
+                a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                torch.cuda.synchronize()
+                a0.record(sa.stream)
+                uT = sa.run_checkpointed(u0a, 0.0, n, K)
+                a1.record(sa.stream)
+                grads = sa.adjoint(uT - tgt, 0.0, n, K)
+                a2.record(sa.stream)
+                torch.cuda.synchronize()
+            fwd, rev = a0.elapsed_time(a1), a1.elapsed_time(a2)
+            extra["adjoint"] = {"value": sa.dof * n / ((fwd + rev) * 1e-3),
+                                "unit": "DOF-steps/s (checkpointed forward + reverse sweep)",
+                                "forward_ms": fwd, "reverse_ms": rev, "steps": n, "checkpoint_every": K,
+                                "dtype": "f64", "dL_dalpha": grads[1],
+                                "workload": "2D fractional FitzHugh-Nagumo, Neumann, N=256 (257^2 nodes), "
+                                            "loss 0.5||u_T - target||^2"}
+            del sa
+        except Exception as exc:
+            extra["adjoint"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DOF-steps/s", "n_gpus": world, "steps": args.steps,
