@@ -6,6 +6,7 @@ the classical compact scheme, the published Cox-Matthews ETDRK4 coefficients,
 the paper's closed-form amplification factor (Eq. 41), the RK4 reduction, exact
 single-mode decay, and the error tables printed in Section 5 (Tables 1 and 2).
 """
+import itertools
 import math
 import os
 
@@ -287,6 +288,36 @@ def test_separable_3d_eigenmodes_decay_by_closed_form_r13(bc):
         U0 += F
         expect += R ** M * F
     got = s.run([U0], 0.0, M)[0]
+    np.testing.assert_allclose(got, expect, atol=1e-12 * np.abs(U0).max())
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+@pytest.mark.parametrize("Ns", [(2,), (3,), (2, 2), (2, 3), (2, 3, 4), (4, 2, 3)])
+def test_smallest_grids_decay_mode_by_mode(bc, Ns):
+    """Degenerate sizes (one to five unknowns per axis): every separable mode of the grid, superposed with
+    random weights, is scaled by R13(L)^M with L from the closed-form eigenvalues (as in the 3D test above)."""
+    dim = len(Ns)
+    lo, hi = (0.0,) * dim, tuple(1.0 + 0.5 * d for d in range(dim))
+    alpha, kappa, tau, M = 1.7, 0.4, 0.03, 4
+    g = O.Grid(Ns, lo, hi)
+    f, J = O.linear(0.0)
+    s = O.ETDRK4P13(O.Problem(g, bc, [alpha], [kappa], tau, f, dreaction=J, nspecies=1))
+    modes_per_axis = [range(1, N) if bc == O.DIRICHLET else range(0, N + 1) if bc == O.NEUMANN else range(N)
+                      for N in Ns]
+    rng = np.random.default_rng(sum(Ns) + dim)
+    U0 = np.zeros(g.shape(bc))
+    expect = np.zeros_like(U0)
+    for ns in itertools.product(*modes_per_axis):
+        F = rng.standard_normal()
+        for d in reversed(range(dim)):                 # field axes are (z, y, x)
+            F = np.multiply.outer(F, _closed_form_mode(bc, ns[d], Ns[d]))
+        lam = sum(_closed_form_lambda(bc, n, N, (b - a) / N) for n, N, a, b in zip(ns, Ns, lo, hi))
+        L = kappa * tau * lam ** (alpha / 2)
+        R = (24 - 6 * L) / (24 + 18 * L + 6 * L * L + L ** 3)
+        U0 += F
+        expect += R ** M * F
+    got = s.run([U0], 0.0, M)[0]
+    assert got.shape == g.shape(bc)
     np.testing.assert_allclose(got, expect, atol=1e-12 * np.abs(U0).max())
 
 
