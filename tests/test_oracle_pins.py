@@ -629,3 +629,42 @@ def test_cox_matthews_and_p13_agree_to_fifth_order_in_l():
         a, b = O.cox_matthews_coefficients(np.array([L]), tau), O.p13_coefficients(np.array([L]), tau)
         d.append(abs(a["R13"][0] - b["R13"][0]))
     assert d[1] / d[0] == pytest.approx(32.0, rel=0.05)
+
+
+# --------------------------------------------------------------------------
+# Section 5: the error norms every parity test decides by
+# --------------------------------------------------------------------------
+
+def test_relative_error_norms_on_hand_computed_values():
+    """rel_max = max|x - y| / max|y| and rel_l2 = ||x - y||_2 / ||y||_2 over all unknowns of all
+    species, checked on arrays whose norms are worked out by hand.  The differences form a 3-4-5
+    triangle and y a 5-12-13 one, so rel_l2 is exactly 5/13: a dropped square root (25/169), a
+    per-species instead of a global norm, or a norm of x instead of y all give another number."""
+    x = [np.array([[4.0, 12.0]]), np.array([0.0])]
+    y = [np.array([[1.0, 12.0]]), np.array([-4.0])]
+    # |x - y| = (3, 0 | 4): max 4; max|y| = 12  ->  4 / 12
+    assert O.rel_max(x, y) == pytest.approx(1.0 / 3.0, rel=0, abs=1e-16)
+    # ||x - y||^2 = 9 + 16 = 25; ||y||^2 = 1 + 144 + 16 = 161
+    assert O.rel_l2(x, y) == pytest.approx(5.0 / math.sqrt(161.0), rel=0, abs=1e-16)
+    # one species: differences (3, 4), y = (5, 12): rel_l2 = 5/13, rel_max = 4/12
+    assert O.rel_l2([np.array([8.0, 16.0])], [np.array([5.0, 12.0])]) == pytest.approx(5.0 / 13.0, rel=0,
+                                                                                         abs=1e-16)
+    assert O.rel_max([np.array([8.0, 16.0])], [np.array([5.0, 12.0])]) == pytest.approx(1.0 / 3.0, rel=0,
+                                                                                          abs=1e-16)
+    # the norms are not symmetric in their arguments: the reference is the second one
+    assert O.rel_l2([np.array([5.0, 12.0])], [np.array([8.0, 16.0])]) == pytest.approx(
+        5.0 / math.sqrt(320.0), rel=0, abs=1e-16)
+    # the largest difference and the largest reference value may sit in different species
+    assert O.rel_max([np.array([0.0, 10.0]), np.array([7.0])], [np.array([0.0, 10.0]), np.array([2.0])]) == \
+        pytest.approx(0.5, rel=0, abs=1e-16)
+    # equal inputs give zero
+    assert O.rel_max(y, y) == 0.0 and O.rel_l2(y, y) == 0.0
+
+
+def test_test_side_error_norms_agree_with_the_oracle_norms():
+    """The single-array norms in tests/helpers.py, on the same hand-computed values."""
+    from tests.helpers import rel_l2, rel_max
+    assert rel_l2(np.array([8.0, 16.0]), np.array([5.0, 12.0])) == pytest.approx(5.0 / 13.0, rel=0, abs=1e-16)
+    assert rel_max(np.array([8.0, 16.0]), np.array([5.0, 12.0])) == pytest.approx(1.0 / 3.0, rel=0, abs=1e-16)
+    assert rel_max(np.array([[0.0, 10.0], [7.0, 0.0]]), np.array([[0.0, 10.0], [2.0, 0.0]])) == \
+        pytest.approx(0.5, rel=0, abs=1e-16)
