@@ -252,12 +252,15 @@ int sfrd_inverse(sfrd_plan_t plan, const void* uhat, void* u);
  * uhat are caller-owned device fields [S][...] (same layout and result as
  * sfrd_forward); stream is a cudaStream_t (NULL: legacy default stream).
  * The first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call on each device before
- * any stream capture is in progress.  Every call shares the array and leaves its
+ * device, with the device current).  Every call copies the plan's tables from
+ * pageable host memory and synchronises the stream, so no call may be made on
+ * a capturing stream or while a global-mode stream capture is in progress.
+ * Every call shares the array and leaves its
  * contents behind; the call clears what must start at zero.  Calls that
  * overlap on the GPU (other streams, other threads) race on the array, and the
  * plan must not be used by another thread during the call.  Synchronises the
- * stream.  Errors: SFRD_EUNSUPPORTED when the plan's scratch exceeds 16 MiB,
+ * stream, also when a launch or copy failed part way.  A bound plan stays
+ * bound: its workspace, stream and tables are untouched.  Errors: SFRD_EUNSUPPORTED when the plan's scratch exceeds 16 MiB,
  * SFRD_ECUDA, SFRD_EINVAL. */
 int sfrd_forward_noalloc(sfrd_plan_t plan, const void* u, void* uhat, void* stream);
 

@@ -104,7 +104,10 @@ extern "C" int sfrd_forward_noalloc(sfrd_plan_t plan, const void* u, void* uhat,
     if (e == cudaSuccess) e = p.dtype == SFRD_F32 ? prepare_kernels<float>(p) : prepare_kernels<double>(p);
     if (e == cudaSuccess)
         e = p.dtype == SFRD_F32 ? launch_forward<float>(p, u, uhat, s) : launch_forward<double>(p, u, uhat, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // wait for the work queued on the shared array even when a launch or copy failed part way, so that
+    // no kernel of this call is still using the array when the call returns
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = es;
 
     p.ws = save_ws;
     p.stream = save_stream;

@@ -39,7 +39,8 @@ class Guarded:
 
 CASES = [(2, (64, 48), "neumann", "fhn"), (2, (96, 200), "periodic", "gray_scott"),
          (3, (16, 12, 10), "dirichlet", "schnakenberg"), (3, (64, 64, 64), "periodic", "gray_scott"),
-         (1, (64,), "dirichlet", "fhn"), (1, (100,), "neumann", "gierer_meinhardt")]
+         (1, (64,), "dirichlet", "fhn"), (1, (100,), "neumann", "gierer_meinhardt"),
+         (2, (64, 1024), "periodic", "gray_scott"), (2, (64, 1024), "neumann", "fhn")]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

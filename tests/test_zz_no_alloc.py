@@ -69,3 +69,52 @@ def test_noalloc_forward_rejects_problems_beyond_its_scratch():
         assert rc == -2
     finally:
         sf.lib().sfrd_destroy(plan)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-6)])
+def test_noalloc_forward_on_a_bound_plan_leaves_the_plan_bound(dtype, tol):
+    """A caller may also hold a bound plan: the allocation-free call borrows the plan's tables for
+    the duration of the call only, so the bound plan's own transform and time steps afterwards equal
+    those of a fresh plan."""
+    cfg = _cfg(2, (64, 40), "dirichlet")
+    cfg["reaction"] = dict(kind="gray_scott", p=[0.04, 0.06], offset=[0, 0])
+    s = sf.Solver(cfg, dtype=dtype)
+    fresh = sf.Solver(cfg, dtype=dtype)
+    rng = np.random.default_rng(7)
+    u = torch.as_tensor(rng.uniform(0, 1, s.shape)).to(device="cuda", dtype=s.tdtype)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        uhat = torch.empty_like(u)
+        rc = sf.lib().sfrd_forward_noalloc(s.handle, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(uhat.data_ptr()),
+                                           stream)
+        assert rc == 0, sf.lib().sfrd_last_error()
+        assert _rel_max(uhat, fresh.forward(u)) < tol
+    torch.testing.assert_close(s.forward(u), fresh.forward(u), rtol=0, atol=0)
+    torch.testing.assert_close(s.run(u, nsteps=3), fresh.run(u, nsteps=3), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+def test_noalloc_forward_1d_and_writes_only_its_output(bc):
+    """1D plans (the transform is the x pass alone), with the output between guard bands of a known byte
+    pattern: the call writes the whole output and nothing next to it."""
+    cfg = _cfg(1, (128,), bc)
+    bound = sf.Solver(cfg, dtype="f64")
+    r = cfg["reaction"]
+    plan = sf.make_plan(1, cfg["N"], cfg["lo"], cfg["hi"], bc, cfg["alpha"], cfg["kappa"], cfg["dt"], "f64",
+                        r["kind"], r["p"], r["offset"], nspecies=2)
+    guard, pattern = 1 << 16, 0xA5
+    nbytes = int(np.prod(bound.shape)) * 8
+    raw = torch.full((2 * guard + nbytes,), pattern, dtype=torch.uint8, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    try:
+        for call in range(2):
+            u = torch.as_tensor(np.random.default_rng(200 + call).uniform(-1, 1, bound.shape)).cuda()
+            rc = sf.lib().sfrd_forward_noalloc(plan, ctypes.c_void_p(u.data_ptr()),
+                                               ctypes.c_void_p(raw.data_ptr() + guard), stream)
+            assert rc == 0, sf.lib().sfrd_last_error()
+            uhat = raw[guard:guard + nbytes].view(torch.float64).reshape(bound.shape)
+            assert _rel_max(uhat, bound.forward(u)) < 1e-12
+            host = raw.cpu().numpy()
+            assert (host[:guard] == pattern).all() and (host[guard + nbytes:] == pattern).all()
+    finally:
+        sf.lib().sfrd_destroy(plan)
