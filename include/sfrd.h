@@ -83,7 +83,11 @@ extern "C" {
  *                      u = e^{-t} sin^3(2 pi x) (one kappa); 1 species, 1D.
  * For SCHNAKENBERG and GIERER_MEINHARDT, U = u + offset[0], V = v + offset[1]:
  * the solver integrates the perturbation about (offset[0], offset[1]); with
- * Dirichlet BCs the boundary condition applies to that perturbation. */
+ * Dirichlet BCs the boundary condition applies to that perturbation.  The
+ * Schnakenberg terms are evaluated expanded about the offset (their value at
+ * the offset taken in FP64 at plan time, plus terms of the perturbation's
+ * size), so that a small perturbation about the steady state keeps its
+ * relative accuracy in FP32. */
 #define SFRD_REACT_NONE              0
 #define SFRD_REACT_LINEAR            1
 #define SFRD_REACT_FHN               2
@@ -143,7 +147,8 @@ int sfrd_plan(sfrd_plan_t* out, const sfrd_grid* grid, int32_t bc,
  *                        coefficients keep FP32 accuracy; 2 (shared) or 4 words
  *                        per unknown and step instead of 10.
  * Call before sfrd_bind (it changes sfrd_workspace_bytes).  SFRD_COEF_RATIONAL
- * needs an FP32 plan whose axes all have power-of-two N in [64, 1024]; such a
+ * needs an FP32 plan whose axes all run on the register engine (N a power of
+ * two in [64, 1024], or 96, 200 or 384); such a
  * plan has no adjoint (sfrd_adjoint* return SFRD_EUNSUPPORTED) and
  * sfrd_coefficients evaluates the rationals from the stored L.
  * Errors: SFRD_EINVAL (mode), SFRD_EUNSUPPORTED, SFRD_ESTATE (already bound). */
@@ -166,7 +171,8 @@ int sfrd_set_coefficients(sfrd_plan_t plan, int32_t mode);
 int sfrd_set_scheme(sfrd_plan_t plan, int32_t scheme);
 
 /* Autotuner of the radix/tile schedule: for the axes on the shared-memory
- * engine (lengths that are not powers of two), times `steps` steps with every
+ * engine (lengths other than the register engine's: powers of two 64..1024,
+ * 96, 200, 384), times `steps` steps with every
  * tile width and radix-stage order (as factored, reversed, ascending,
  * descending) and keeps the fastest.  With the environment variable
  * SFRD_AUTOTUNE_CACHE naming a file, a choice recorded there for the same grid,
@@ -279,9 +285,9 @@ int sfrd_coefficients(sfrd_plan_t plan, int32_t which, void* out);
 int sfrd_profile_step(sfrd_plan_t plan, int32_t cap, float* ms, int32_t* kind);
 
 /* ---- discrete adjoint (gradients through nsteps steps) ---------------------
- * Available when every axis length N is a power of two in [64, 1024]
- * (SFRD_EUNSUPPORTED otherwise).  The adjoint is the exact transpose of the
- * library's own FP arithmetic path (transposed transforms, the same
+ * Available when every axis runs on the register engine: N a power of two in
+ * [64, 1024], or 96, 200 or 384 (SFRD_EUNSUPPORTED otherwise).  The adjoint is
+ * the exact transpose of the library's own FP arithmetic path (transposed transforms, the same
  * coefficient arrays, the reaction Jacobian transposed), i.e. the gradient of
  * the discrete map u0 -> u(t0 + nsteps tau) of Eq. ETDRK4P13.
  *

@@ -24,11 +24,17 @@ __device__ __forceinline__ void react2k(int kind, const ReactDev& re, T u, T v, 
             fv = uvv - (F + K) * v;
         } break;
         case SFRD_REACT_SCHNAKENBERG: {
-            const T g = (T)re.p[0], a = (T)re.p[1], b = (T)re.p[2];
-            const T U = u + (T)re.off[0], V = v + (T)re.off[1];
-            const T uuv = U * U * V;
-            fu = g * (a - U + uuv);
-            fv = g * (b - uuv);
+            // f at (U, V) = (u0 + u, v0 + v), the perturbation (u, v) about the offset: with
+            // q = U^2 V - u0^2 v0 = v0 u (2 u0 + u) + v U^2,
+            //   f_u = g (a - U + U^2 V) = g (c0 - u + q),   f_v = g (b - U^2 V) = g (c1 - q),
+            // c0 = a - u0 + u0^2 v0 and c1 = b - u0^2 v0 taken in FP64 at plan time (both zero at the
+            // homogeneous steady state).  Every term is of the size of the perturbation, so the
+            // O(1) parts of a - U + U^2 V do not cancel in the run precision.
+            const T g = (T)re.p[0], u0 = (T)re.off[0], v0 = (T)re.off[1];
+            const T U = u0 + u;
+            const T q = v0 * u * ((T)2 * u0 + u) + v * U * U;
+            fu = g * ((T)re.c[0] - u + q);
+            fv = g * ((T)re.c[1] - q);
         } break;
         case SFRD_REACT_GIERER_MEINHARDT: {
             const T U = u + (T)re.off[0], V = v + (T)re.off[1];
@@ -111,11 +117,12 @@ __device__ __forceinline__ void react2_vjp(const ReactDev& re, T u, T v, T yu, T
             dp[1] += w * (double)(-v * yv);
         } break;
         case SFRD_REACT_SCHNAKENBERG: {
-            const T g = (T)re.p[0], a = (T)re.p[1], b = (T)re.p[2];
+            const T g = (T)re.p[0];
             const T U = u + (T)re.off[0], V = v + (T)re.off[1];
             gu = g * (-(T)1 + (T)2 * U * V) * yu - g * (T)2 * U * V * yv;
             gv = g * U * U * yu - g * U * U * yv;
-            dp[0] += w * (double)((a - U + U * U * V) * yu + (b - U * U * V) * yv);
+            const T q = (T)re.off[1] * u * ((T)2 * (T)re.off[0] + u) + v * U * U;   // as in react2k
+            dp[0] += w * (double)(((T)re.c[0] - u + q) * yu + ((T)re.c[1] - q) * yv);
             dp[1] += w * (double)(g * yu);
             dp[2] += w * (double)(g * yv);
         } break;

@@ -192,10 +192,10 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
             p->n[d] = unknowns(bc, g->N[d]);
             const long long N = g->N[d];
             const long long M = bc == SFRD_BC_PERIODIC ? N : 2 * N;
-            // power-of-two lengths up to 1024 run on the register engine (its tables have length M);
-            // other lengths need a {2,3,5}-smooth M <= 1024 for the shared-memory engine
-            const bool pow2ok = N >= v2::kMinN && N <= v2::kMaxN && (N & (N - 1)) == 0;
-            if ((!pow2ok && M > kMaxFFT) || !factor((int)M, p->radix[d])) {
+            // the register engine's lengths (powers of two up to 1024, and 96, 200, 384) take tables of
+            // length M; other lengths need a {2,3,5}-smooth M <= 1024 for the shared-memory engine
+            const bool regok = v2::reg_len(N);
+            if ((!regok && M > kMaxFFT) || !factor((int)M, p->radix[d])) {
                 delete p;
                 return SFRD_EUNSUPPORTED;
             }
@@ -212,7 +212,7 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
         const bool generic = eng && std::strcmp(eng, "generic") == 0;
         for (int d = 0; d < g->dim; ++d) {
             const long long N = p->Nint[d];
-            p->v2[d] = !generic && N >= v2::kMinN && N <= v2::kMaxN && (N & (N - 1)) == 0;
+            p->v2[d] = !generic && v2::reg_len(N);
         }
     }
     p->pitch = (p->n[0] + 3) / 4 * 4;
@@ -230,6 +230,14 @@ int create_plan(Plan** out, const sfrd_grid* g, int bc, const double* alpha, con
     for (int i = 0; i < 8; ++i) p->re.p[i] = re->p[i];
     p->re.off[0] = re->offset[0];
     p->re.off[1] = re->offset[1];
+    p->re.c[0] = p->re.c[1] = 0.0;
+    if (re->kind == SFRD_REACT_SCHNAKENBERG) {
+        // the reaction at the offset: zero at the homogeneous steady state, so that the kernels add only
+        // terms of the size of the perturbation (see reaction.cuh)
+        const double u0 = re->offset[0], v0 = re->offset[1];
+        p->re.c[0] = re->p[1] - u0 + u0 * u0 * v0;
+        p->re.c[1] = re->p[2] - u0 * u0 * v0;
+    }
     if (re->kind == SFRD_REACT_FISHER_MMS) {
         const double a = alpha[0], k = kappa[0];
         p->re.p[0] = k / 4.0 * 3.0 * std::pow(2.0 * M_PI, a);

@@ -33,6 +33,7 @@ struct ReactDev {
     int S;
     double p[8];
     double off[2];
+    double c[2];   // Schnakenberg: (a - u0 + u0^2 v0, b - u0^2 v0) at the offset (u0, v0), in FP64
 };
 
 // Device-resident clock: t_k = t0 + k tau (Algorithm 1).
@@ -190,6 +191,11 @@ template <typename T> cudaError_t prepare_kernels(const Plan& p);
 namespace v2 {
 constexpr int kMaxDynSmem2 = 227 * 1024;
 constexpr int kMinN = 64, kMaxN = 1024;
+// Axis lengths (intervals) with a register-engine split: the powers of two 64..1024 and the
+// 3 * 2^k / 5^2 * 2^k lengths 96, 200, 384.
+constexpr bool reg_len(long long N) {
+    return (N >= kMinN && N <= kMaxN && (N & (N - 1)) == 0) || N == 96 || N == 200 || N == 384;
+}
 // Columns per tile of the register engine (kept in sync with fft2.cuh's TileCC).
 constexpr int cc_for(bool f64, int N) { return f64 ? (N >= 1024 ? 4 : 8) : (N >= 1024 ? 8 : 16); }
 template <typename T, int N> cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s);
