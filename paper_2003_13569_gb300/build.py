@@ -33,14 +33,27 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def _newest_header():
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    hdrs += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
+    return max(os.path.getmtime(h) for h in hdrs)
+
+
 def build(verbose=False, extra=()):
+    """Compile every translation unit (in parallel) and link libsfrd.so.  With SFRD_BUILD_INCREMENTAL=1
+    an object newer than its source and every header is reused (a local convenience; a fresh
+    checkout always compiles everything)."""
     nvcc = nvcc_path()
     os.makedirs(BUILD_DIR, exist_ok=True)
+    incremental = os.environ.get("SFRD_BUILD_INCREMENTAL") == "1"
+    newest_hdr = _newest_header() if incremental else 0.0
     procs = []
     objs = []
     for src in sources():
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
+        if incremental and os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(src), newest_hdr):
+            continue
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)

@@ -1,0 +1,168 @@
+// Persistent kernels of the batched step, one per engine length and pass mode.
+//
+// A batched pass runs the instances whose pass axis has the same length on the
+// register engine as one launch of a kernel compiled for that length (its
+// register budget and tile exactly those of the single-instance pass), and the
+// instances on the shared-memory engine as one launch of the generic kernel.
+// Every block of a launch takes (instance, tile) work items from the launch's
+// own device counter, copies the instance's pass arguments into shared memory
+// and runs the single-instance device body on that tile.
+#pragma once
+
+#include "passes2.cuh"
+
+namespace sfrd {
+
+struct BatchItem {
+    int inst, bx, by, cost;
+};
+
+template <typename T> struct BatchX {
+    XArgs<T> a;
+    int engine;   // 1 register engine, 0 shared-memory engine
+    int N;
+};
+
+template <typename T> struct BatchC {
+    ColArgs<T> a;
+    int engine;
+    int N;
+};
+
+// Pass kinds of a batched launch.
+enum BatchAxis { BATCH_X = 0, BATCH_COL = 1 };
+
+template <typename A>
+__device__ __forceinline__ void copy_args(A* dst, const A* src) {
+    static_assert(sizeof(A) % 4 == 0, "argument block must be word sized");
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(A) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+// The work loop of one persistent block: body(args, item) for every item it takes.  The x pass
+// (XPASS) sets the stage fraction of the reaction time in the copied arguments.
+template <bool XPASS, typename Args, typename Inst, class Body>
+__device__ __forceinline__ void batch_loop(const Inst* __restrict__ insts, const BatchItem* __restrict__ items,
+                                           int nitems, int* counter, double frac, Args* s_args, int* s_w,
+                                           Body&& body) {
+    for (;;) {
+        if (threadIdx.x == 0) *s_w = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = *s_w;
+        if (w >= nitems) break;
+        const BatchItem it = items[w];
+        copy_args(s_args, &insts[it.inst].a);
+        __syncthreads();
+        if constexpr (XPASS) {
+            if (threadIdx.x == 0) s_args->stage_frac = frac;
+            __syncthreads();
+        }
+        body(*s_args, it);
+        __syncthreads();
+    }
+}
+
+namespace v2 {
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>()))
+    batch_x2_kernel(const BatchX<T>* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
+                    double stage_frac, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) XArgs<T> s_args;
+    __shared__ int s_w;
+    batch_loop<true>(insts, items, nitems, counter, stage_frac, &s_args, &s_w,
+               [&](const XArgs<T>& a, const BatchItem& it) { x2_body<T, N, MODE>(a, it.bx, smem_raw); });
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>()))
+    batch_col2_kernel(const BatchC<T>* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
+                      int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) ColArgs<T> s_args;
+    __shared__ int s_w;
+    batch_loop<false>(insts, items, nitems, counter, 0.0, &s_args, &s_w, [&](const ColArgs<T>& a, const BatchItem& it) {
+        col2_body<T, N, MODE>(a, it.bx, it.by, smem_raw);
+    });
+}
+
+// Grid of a persistent launch: blocks_per_sm resident blocks per SM (0: as many as fit), never more than
+// the launch's items.
+inline int batch_grid(const void* kernel, size_t smem, int blocks_per_sm, int sms, int nitems, cudaError_t* err) {
+    int occ = 0;
+    *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem);
+    if (occ < 1) occ = 1;
+    const int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
+    const long long g = (long long)bps * sms;
+    return (int)(g < nitems ? g : nitems);
+}
+
+// Kernel of the length-N batched pass of kind `axis` and `mode`.
+template <typename T, int N>
+const void* batch_kernel2(int axis, int mode) {
+    if (axis == BATCH_X) return reinterpret_cast<const void*>(batch_x2_kernel<T, N, MODE_REACT>);
+    switch (mode) {
+        case MODE_PLAIN: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_PLAIN>);
+        case MODE_TA: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TA>);
+        case MODE_TB: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TB>);
+        case MODE_TC: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TC>);
+        default: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TD>);
+    }
+}
+
+// Grids of the length-N batched launches (taken when the batch is bound, outside any capture):
+// grid[0] the x pass, grid[1 + m] the column pass of mode m in (PLAIN, TA, TB, TC, TD).
+template <typename T, int N>
+cudaError_t batch_grids2(int axis, int blocks_per_sm, int sms, int nitems, int* grid) {
+    const size_t smem = TileOf<T, N>::E::smem_bytes();
+    cudaError_t e = cudaSuccess;
+    if (axis == BATCH_X) {
+        grid[0] = batch_grid(batch_kernel2<T, N>(BATCH_X, MODE_REACT), smem, blocks_per_sm, sms, nitems, &e);
+        return e;
+    }
+    const int modes[5] = {MODE_PLAIN, MODE_TA, MODE_TB, MODE_TC, MODE_TD};
+    for (int m = 0; m < 5 && e == cudaSuccess; ++m)
+        grid[1 + m] = batch_grid(batch_kernel2<T, N>(BATCH_COL, modes[m]), smem, blocks_per_sm, sms, nitems, &e);
+    return e;
+}
+
+// One launch of the length-N kernel of pass kind `axis` and `mode` on stream s, `grid` blocks.
+template <typename T, int N>
+cudaError_t batch_launch2(int axis, int mode, const void* args, const BatchItem* items, int nitems, double frac,
+                          int* counter, int grid, cudaStream_t s) {
+    const size_t smem = TileOf<T, N>::E::smem_bytes();
+    if (axis == BATCH_X) {
+        batch_x2_kernel<T, N, MODE_REACT><<<grid, kThreads, smem, s>>>(static_cast<const BatchX<T>*>(args), items,
+                                                                       nitems, frac, counter);
+        return cudaGetLastError();
+    }
+    auto k = reinterpret_cast<void (*)(const BatchC<T>*, const BatchItem*, int, int*)>(
+        const_cast<void*>(batch_kernel2<T, N>(BATCH_COL, mode)));
+    k<<<grid, kThreads, smem, s>>>(static_cast<const BatchC<T>*>(args), items, nitems, counter);
+    return cudaGetLastError();
+}
+
+// Shared-memory size attribute of the length-N batched kernels.
+template <typename T, int N>
+cudaError_t batch_prepare2() {
+    const int m = (int)TileOf<T, N>::E::smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(batch_x2_kernel<T, N, MODE_REACT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+    void (*ks[])(const BatchC<T>*, const BatchItem*, int, int*) = {
+        batch_col2_kernel<T, N, MODE_PLAIN>, batch_col2_kernel<T, N, MODE_TA>, batch_col2_kernel<T, N, MODE_TB>,
+        batch_col2_kernel<T, N, MODE_TC>, batch_col2_kernel<T, N, MODE_TD>};
+    for (auto k : ks)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+    return e;
+}
+
+#define SFRD_BATCH_INSTANTIATE(T, N)                                                                     \
+    template cudaError_t batch_grids2<T, N>(int, int, int, int, int*);                                    \
+    template cudaError_t batch_launch2<T, N>(int, int, const void*, const BatchItem*, int, double, int*, int, \
+                                             cudaStream_t);                                               \
+    template cudaError_t batch_prepare2<T, N>();
+
+}  // namespace v2
+}  // namespace sfrd

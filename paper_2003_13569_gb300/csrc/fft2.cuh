@@ -1,4 +1,5 @@
-// Register FFT engine for power-of-two axis lengths N (16 <= N <= 1024).
+// Register FFT engine for the axis lengths N with an in-register split N = R1 x R2 (Split<N>):
+// the powers of two 16..1024 and 96, 200, 384.
 //
 // Each real transform of the solver (Section 3.1: Hartley for periodic axes,
 // DST-I for Dirichlet, DCT-I for Neumann) is computed from ONE complex FFT of
@@ -87,21 +88,21 @@ constexpr CS ce_cs2pi(long m, long R) {
     }
 }
 
-// a * omega_32^M, omega_32 = exp(-2 pi i / 32), with M a compile-time constant: the quarter
-// turns are exchanges and sign changes, the rest multiplies by literal constants.
-template <int M, typename C> __device__ __forceinline__ C mul_w32(C a) {
+// a * omega_R^M, omega_R = exp(-2 pi i / R), M and R compile-time constants (quarter turns as
+// exchanges and sign changes when 4 divides R).
+template <int M, int R, typename C> __device__ __forceinline__ C mul_wr(C a) {
     using T = decltype(a.x);
-    constexpr int m = ((M % 32) + 32) % 32;
+    constexpr int m = ((M % R) + R) % R;
     if constexpr (m == 0) {
         return a;
-    } else if constexpr (m == 8) {
+    } else if constexpr (R % 4 == 0 && m == R / 4) {
         return mul_mi(a);
-    } else if constexpr (m == 16) {
+    } else if constexpr (R % 2 == 0 && m == R / 2) {
         return cneg(a);
-    } else if constexpr (m == 24) {
+    } else if constexpr (R % 4 == 0 && m == 3 * R / 4) {
         C r; r.x = -a.y; r.y = a.x; return r;
     } else {
-        constexpr T wr = (T)ce_cs2pi(m, 32).c, wi = (T)(-ce_cs2pi(m, 32).s);
+        constexpr T wr = (T)ce_cs2pi(m, R).c, wi = (T)(-ce_cs2pi(m, R).s);
         C r; r.x = a.x * wr - a.y * wi; r.y = a.x * wi + a.y * wr; return r;
     }
 }
@@ -133,7 +134,7 @@ template <int R, int Ra, typename C> struct FourStep {
             RDft<Ra, C>::run(u);
             static_for<0, Ra>([&](auto K1) {
                 constexpr int k1 = decltype(K1)::value;
-                t[j2 * Ra + k1] = mul_w32<j2 * k1 * (32 / R)>(u[k1]);
+                t[j2 * Ra + k1] = mul_wr<j2 * k1, R>(u[k1]);
             });
         });
 #pragma unroll
@@ -154,6 +155,22 @@ template <typename C> struct RDft<16, C> {
 template <typename C> struct RDft<32, C> {
     static __device__ __forceinline__ void run(C* a) { FourStep<32, 8, C>::run(a); }
 };
+// composite lengths with factors 3 and 5 (the non-power-of-two axis lengths of the engine)
+template <typename C> struct RDft<6, C> {
+    static __device__ __forceinline__ void run(C* a) { FourStep<6, 2, C>::run(a); }
+};
+template <typename C> struct RDft<10, C> {
+    static __device__ __forceinline__ void run(C* a) { FourStep<10, 2, C>::run(a); }
+};
+template <typename C> struct RDft<12, C> {
+    static __device__ __forceinline__ void run(C* a) { FourStep<12, 4, C>::run(a); }
+};
+template <typename C> struct RDft<20, C> {
+    static __device__ __forceinline__ void run(C* a) { FourStep<20, 4, C>::run(a); }
+};
+template <typename C> struct RDft<24, C> {
+    static __device__ __forceinline__ void run(C* a) { FourStep<24, 8, C>::run(a); }
+};
 
 // ---- the line engine ----------------------------------------------------------------
 
@@ -165,6 +182,10 @@ template <> struct Split<128> { static constexpr int R1 = 8, R2 = 16; };
 template <> struct Split<256> { static constexpr int R1 = 16, R2 = 16; };
 template <> struct Split<512> { static constexpr int R1 = 16, R2 = 32; };
 template <> struct Split<1024> { static constexpr int R1 = 32, R2 = 32; };
+// 3 * 2^5, 5^2 * 2^3 and 3 * 2^7 (the Gierer-Meinhardt batch's other sides)
+template <> struct Split<96> { static constexpr int R1 = 6, R2 = 16; };
+template <> struct Split<200> { static constexpr int R1 = 10, R2 = 20; };
+template <> struct Split<384> { static constexpr int R1 = 16, R2 = 24; };
 
 // Columns per tile for a power-of-two axis length.
 template <typename T, int N> struct TileCC { static constexpr int value = cc_for(sizeof(T) == 8, N); };
@@ -241,13 +262,14 @@ struct Eng {
                 RDft<R1, C>::run(a[o]);
                 if (R1 <= 16) {
                     // omega_N^{n2 k1} = (omega_N^{4 n2})^{k1 / 4} (omega_N^{n2})^{k1 % 4}: two table reads
-                    C pw[4], qw[R1 / 4];
+                    constexpr int NQ = (R1 + 3) / 4;
+                    C pw[4], qw[NQ > 1 ? NQ : 2];
                     pw[1] = tws[n2 * twstride];
                     pw[2] = cmul(pw[1], pw[1]);
                     pw[3] = cmul(pw[2], pw[1]);
-                    if (R1 / 4 > 1) qw[1] = tws[4 * n2 * twstride];
-                    if (R1 / 4 > 2) qw[2] = cmul(qw[1], qw[1]);
-                    if (R1 / 4 > 3) qw[3] = cmul(qw[2], qw[1]);
+                    if (NQ > 1) qw[1] = tws[4 * n2 * twstride];
+                    if (NQ > 2) qw[2] = cmul(qw[1], qw[1]);
+                    if (NQ > 3) qw[3] = cmul(qw[2], qw[1]);
 #pragma unroll
                     for (int k1 = 1; k1 < R1; ++k1) {
                         const int qq = k1 / 4, r = k1 % 4;
@@ -303,7 +325,7 @@ struct Eng {
             const int k = k0 + t;
             if (k < H) {
                 const C zk = buf[k * LD + c];
-                const C zm = buf[((N - k) & (N - 1)) * LD + c];
+                const C zm = buf[((N & (N - 1)) == 0 ? ((N - k) & (N - 1)) : (k == 0 ? 0 : N - k)) * LD + c];
                 const C Rk = cscale(cadd(zk, zm), (T)0.5);
                 const C d = csub(zk, zm);
                 C Ik;

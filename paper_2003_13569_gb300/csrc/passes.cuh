@@ -465,6 +465,9 @@ cudaError_t prepare_kernels(const Plan& p) {
             case 128: SFRD_TRY((v2::prepare2<T, 128>())); SFRD_TRY((v2::prepare_adj<T, 128>())); break;
             case 256: SFRD_TRY((v2::prepare2<T, 256>())); SFRD_TRY((v2::prepare_adj<T, 256>())); break;
             case 512: SFRD_TRY((v2::prepare2<T, 512>())); SFRD_TRY((v2::prepare_adj<T, 512>())); break;
+            case 96: SFRD_TRY((v2::prepare2<T, 96>())); SFRD_TRY((v2::prepare_adj<T, 96>())); break;
+            case 200: SFRD_TRY((v2::prepare2<T, 200>())); SFRD_TRY((v2::prepare_adj<T, 200>())); break;
+            case 384: SFRD_TRY((v2::prepare2<T, 384>())); SFRD_TRY((v2::prepare_adj<T, 384>())); break;
             default: SFRD_TRY((v2::prepare2<T, 1024>())); SFRD_TRY((v2::prepare_adj<T, 1024>())); break;
         }
     }
@@ -604,6 +607,9 @@ static cudaError_t launch_col(const Plan& p, int d, int mode, const ColArgs<T>& 
             case 128: return adj ? v2::adj_col_launch<T, 128>(a, mode, grid, s) : v2::col2_launch<T, 128>(a, mode, grid, s);
             case 256: return adj ? v2::adj_col_launch<T, 256>(a, mode, grid, s) : v2::col2_launch<T, 256>(a, mode, grid, s);
             case 512: return adj ? v2::adj_col_launch<T, 512>(a, mode, grid, s) : v2::col2_launch<T, 512>(a, mode, grid, s);
+            case 96: return adj ? v2::adj_col_launch<T, 96>(a, mode, grid, s) : v2::col2_launch<T, 96>(a, mode, grid, s);
+            case 200: return adj ? v2::adj_col_launch<T, 200>(a, mode, grid, s) : v2::col2_launch<T, 200>(a, mode, grid, s);
+            case 384: return adj ? v2::adj_col_launch<T, 384>(a, mode, grid, s) : v2::col2_launch<T, 384>(a, mode, grid, s);
             default: return adj ? v2::adj_col_launch<T, 1024>(a, mode, grid, s) : v2::col2_launch<T, 1024>(a, mode, grid, s);
         }
     }
@@ -659,6 +665,9 @@ static cudaError_t launch_x(const Plan& p, int mode, const XArgs<T>& a, dim3 gri
             case 128: return adj ? v2::adj_x_launch<T, 128>(a, grid, s) : v2::x2_launch<T, 128>(a, mode, grid, s);
             case 256: return adj ? v2::adj_x_launch<T, 256>(a, grid, s) : v2::x2_launch<T, 256>(a, mode, grid, s);
             case 512: return adj ? v2::adj_x_launch<T, 512>(a, grid, s) : v2::x2_launch<T, 512>(a, mode, grid, s);
+            case 96: return adj ? v2::adj_x_launch<T, 96>(a, grid, s) : v2::x2_launch<T, 96>(a, mode, grid, s);
+            case 200: return adj ? v2::adj_x_launch<T, 200>(a, grid, s) : v2::x2_launch<T, 200>(a, mode, grid, s);
+            case 384: return adj ? v2::adj_x_launch<T, 384>(a, grid, s) : v2::x2_launch<T, 384>(a, mode, grid, s);
             default: return adj ? v2::adj_x_launch<T, 1024>(a, grid, s) : v2::x2_launch<T, 1024>(a, mode, grid, s);
         }
     }

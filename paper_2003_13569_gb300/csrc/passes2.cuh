@@ -13,13 +13,25 @@
 namespace sfrd {
 namespace v2 {
 
-// Blocks per SM the register allocation is sized for: 64 registers per thread for FP32 lines up
-// to 256 (80 for the update pass, whose batches carry eight values per element), 128 for longer
-// lines and for FP64, 255 for FP64 at 512-1024.
+// Complex values a thread holds in one FFT step: the larger of step 1 (R1 per owner n2) and step 2
+// (R2 per owner k1) over the tile's groups.
+template <typename T, int N>
+constexpr int fft_values() {
+    constexpr int G = kThreads / cc_for(sizeof(T) == 8, N);
+    constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2;
+    constexpr int v1 = (R2 + G - 1) / G * R1, v2 = (R1 + G - 1) / G * R2;
+    return v1 > v2 ? v1 : v2;
+}
+
+// Blocks per SM the register allocation is sized for.  FP32: 64 registers per thread when a thread
+// holds at most 16 complex values per FFT step (80 for the update pass, whose batches carry eight
+// values per element), 80 up to 20 values, 128 beyond (the 24- and 32-value steps of 384-1024).
+// FP64: 128 registers up to 20 values, 255 beyond.
 template <typename T, int N, int MODE>
 constexpr int min_blocks() {
-    return sizeof(T) == 8 ? (N >= 512 ? 1 : 2)
-                          : (N >= 512 ? 2 : (MODE == MODE_TD ? 3 : 4));
+    return sizeof(T) == 8 ? (fft_values<T, N>() > 20 ? 1 : 2)
+                          : (fft_values<T, N>() > 20 ? 2
+                                                     : (fft_values<T, N>() > 16 || MODE == MODE_TD ? 3 : 4));
 }
 
 template <typename T, int N, int BCT = -1>

@@ -37,6 +37,13 @@ void drop_graph(BatchPlan& b) {
     b.graph = nullptr;
 }
 
+void drop_streams(BatchPlan& b) {
+    for (cudaStream_t s : b.side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b.join) cudaEventDestroy(e);
+    b.side.clear();
+    b.join.clear();
+}
+
 cudaError_t step_direct(BatchPlan& b, cudaStream_t s) {
     return b.dtype == SFRD_F32 ? sfrd::batch_step<float>(b, s) : sfrd::batch_step<double>(b, s);
 }
@@ -88,9 +95,9 @@ int sfrd_batch_plan(sfrd_batch_t* out, int64_t count, const sfrd_grid* grids, co
     size_t items = 0;
     for (const Plan& p : b.inst) items += (size_t)(p.n[1] * p.n[2] + 1) + 3 * (size_t)(p.pitch + 1) * (p.n[1] + p.n[2] + 1);
     b.off_tables = o;    // pass tables start here (filled at bind)
-    o = up256(o + count * per_inst + items * sizeof(sfrd::BatchItem) + 8 * 256);
+    o = up256(o + count * per_inst + items * sizeof(sfrd::BatchItem) + 64 * 256);
     b.off_counters = o;
-    o = up256(o + 64 * sizeof(int));
+    o = up256(o + sfrd::kBatchCounters * sizeof(int));
     b.ws_bytes = o;
     *out = h;
     return SFRD_OK;
@@ -122,15 +129,27 @@ int sfrd_batch_bind(sfrd_batch_t batch, void* workspace, size_t bytes, void* str
     if (base + host.size() > b.off_counters) return SFRD_EUNSUPPORTED;
     for (sfrd::BatchPass* ps : {&b.px, &b.pmid, &b.pslow}) {
         ps->off_args += base;
-        ps->off_items += base;
+        for (sfrd::BatchGroup& gr : ps->groups) gr.off_items += base;
     }
     SFRD_BCUDA(cudaMemcpyAsync(b.ws + base, host.data(), host.size(), cudaMemcpyHostToDevice, b.stream));
     SFRD_BCUDA(b.dtype == SFRD_F32 ? sfrd::batch_prepare<float>() : sfrd::batch_prepare<double>());
-    int dev = 0, sms = 0;
+    int dev = 0;
     SFRD_BCUDA(cudaGetDevice(&dev));
-    SFRD_BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    b.max_blocks = (b.blocks_per_sm > 0 ? b.blocks_per_sm : 2) * sms;
+    SFRD_BCUDA(cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, dev));
     if (!b.cap_stream) SFRD_BCUDA(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
+    SFRD_BCUDA(b.dtype == SFRD_F32 ? sfrd::batch_set_grids<float>(b) : sfrd::batch_set_grids<double>(b));
+    // side streams and events for the launch groups of a pass (forked and joined inside the step graph)
+    const int ng = sfrd::batch_max_groups(b.inst, b.dim);
+    while ((int)b.side.size() < ng) {
+        cudaStream_t st = nullptr;
+        SFRD_BCUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b.side.push_back(st);
+    }
+    while ((int)b.join.size() < ng + 1) {
+        cudaEvent_t ev = nullptr;
+        SFRD_BCUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b.join.push_back(ev);
+    }
     SFRD_BCUDA(cudaStreamSynchronize(b.stream));
     return SFRD_OK;
 }
@@ -195,7 +214,7 @@ int sfrd_batch_info(sfrd_batch_t batch, int64_t* count, int64_t* dof, int64_t* l
     for (const Plan& p : b.inst) d += p.dense * p.S;
     if (count) *count = (int64_t)b.inst.size();
     if (dof) *dof = d;
-    if (launches_per_step) *launches_per_step = b.dim == 3 ? 16 : 8;
+    if (launches_per_step) *launches_per_step = sfrd::batch_launches_per_step(b.inst, b.dim);
     return SFRD_OK;
 }
 
@@ -253,6 +272,7 @@ int sfrd_batch_autotune(sfrd_batch_t batch, int32_t steps, int32_t* chosen) {
 void sfrd_batch_destroy(sfrd_batch_t batch) {
     if (!batch) return;
     drop_graph(batch->b);
+    drop_streams(batch->b);
     if (batch->b.cap_stream) cudaStreamDestroy(batch->b.cap_stream);
     delete batch;
 }

@@ -1,0 +1,8 @@
+// Batched persistent kernels, F32, register-engine axis length 200.
+#include "batch_kernels.cuh"
+
+namespace sfrd {
+namespace v2 {
+SFRD_BATCH_INSTANTIATE(float, 200)
+}  // namespace v2
+}  // namespace sfrd

@@ -1,0 +1,8 @@
+// Batched persistent kernels, F64, register-engine axis length 512.
+#include "batch_kernels.cuh"
+
+namespace sfrd {
+namespace v2 {
+SFRD_BATCH_INSTANTIATE(double, 512)
+}  // namespace v2
+}  // namespace sfrd

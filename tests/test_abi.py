@@ -129,7 +129,7 @@ def test_coefficient_mode_selection_on_the_host(sfrd):
     h64 = _plan(sfrd, N=(64, 64, 1), dtype="f64")
     assert lib.sfrd_set_coefficients(h64, 1) == -2
     lib.sfrd_destroy(h64)
-    hg = _plan(sfrd, N=(96, 64, 1), dtype="f32")          # 96 runs on the shared-memory engine
+    hg = _plan(sfrd, N=(80, 64, 1), dtype="f32")          # 80 runs on the shared-memory engine
     assert lib.sfrd_set_coefficients(hg, 1) == -2
     lib.sfrd_destroy(hg)
     assert lib.sfrd_set_coefficients(None, 1) == -1

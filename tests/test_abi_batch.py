@@ -49,7 +49,7 @@ def test_valid_batch_reports_count_unknowns_and_launches():
     assert code == 0 and h.value
     cnt, dof, lps = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     assert L.sfrd_batch_info(h, ctypes.byref(cnt), ctypes.byref(dof), ctypes.byref(lps)) == 0
-    assert cnt.value == 3 and lps.value == 8
+    assert cnt.value == 3 and lps.value == 4 * 2 * 3        # one launch per axis length and pass
     assert dof.value == 2 * sum(_unknowns(N, b) for N, b in zip(sides, bcs))
     assert L.sfrd_batch_info(h, None, None, None) == 0                 # NULL outputs are skipped
     nb = ctypes.c_size_t()
@@ -58,11 +58,13 @@ def test_valid_batch_reports_count_unknowns_and_launches():
     L.sfrd_batch_destroy(h)
 
 
-def test_3d_batch_has_sixteen_launches_per_step():
+def test_3d_batch_launches_per_step():
+    """Four passes per stage (middle, x, middle, slow), each one launch per engine group: here the
+    shared-memory engine (32 intervals) and the register engine at 64."""
     code, h = _batch([32, 64], ["dirichlet", "neumann"], dims=[3, 3])
     assert code == 0
     lps = ctypes.c_int64()
-    assert L.sfrd_batch_info(h, None, None, ctypes.byref(lps)) == 0 and lps.value == 16
+    assert L.sfrd_batch_info(h, None, None, ctypes.byref(lps)) == 0 and lps.value == 4 * 4 * 2
     L.sfrd_batch_destroy(h)
 
 

@@ -54,7 +54,10 @@ def _rel(a, b):
 
 CASES = [((64, 64), "neumann", "fhn", 2), ((64, 128), "periodic", "gray_scott", 2),
          ((64, 64), "dirichlet", "schnakenberg", 2), ((128, 64), "neumann", "gierer_meinhardt", 2),
-         ((64, 64, 64), "dirichlet", "schnakenberg", 3)]
+         ((64, 64, 64), "dirichlet", "schnakenberg", 3),
+         # register-engine lengths 3 * 2^5, 5^2 * 2^3 and 3 * 2^7
+         ((96, 200), "dirichlet", "fhn", 2), ((200, 96), "periodic", "gierer_meinhardt", 2),
+         ((384, 96), "neumann", "gray_scott", 2)]
 
 
 @pytest.mark.parametrize("N,bc,kind,dim", CASES)
@@ -77,7 +80,7 @@ def test_adjoint_matches_oracle_adjoint(N, bc, kind, dim):
         assert _rel(dp[0], ref["params"]) < 1e-8
 
 
-@pytest.mark.parametrize("N,bc,kind,dim", CASES[:4])
+@pytest.mark.parametrize("N,bc,kind,dim", CASES[:4] + CASES[5:6])
 def test_adjoint_matches_central_differences(N, bc, kind, dim):
     cfg = _cfg(N, bc, kind, dim=dim)
     nsteps, K = 6, 4

@@ -82,7 +82,8 @@ def test_gierer_meinhardt_256_instance_workload_sampled():
     cfgs = W.gm_instances(256, seed=3)
     u0 = [np.stack(W.initial_fields(c)) for c in cfgs]
     b = sf.Batch(cfgs, dtype="f32")
-    assert b.count == 256 and b.launches_per_step == 8
+    # one launch per pass for each axis length (96, 128, 200, 256, 384), 4 stages x 2 passes
+    assert b.count == 256 and b.launches_per_step == 4 * 2 * 5
     b.load(u0)
     b.advance(2)
     got = b.store()

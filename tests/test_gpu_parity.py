@@ -86,7 +86,10 @@ SHAPES_V2 = [(2, (64, 128), "periodic"), (2, (64, 128), "dirichlet"), (2, (64, 1
              (2, (256, 64), "dirichlet"), (2, (256, 64), "neumann"), (2, (512, 64), "periodic"),
              (2, (1024, 64), "periodic"), (2, (1024, 64), "neumann"), (2, (512, 64), "dirichlet"),
              (3, (64, 64, 128), "dirichlet"), (3, (128, 64, 64), "neumann"), (3, (64, 128, 64), "periodic"),
-             (3, (64, 48, 80), "dirichlet")]
+             (3, (64, 48, 80), "dirichlet"),
+             # lengths 3 * 2^5, 5^2 * 2^3, 3 * 2^7 on the register engine (mixed-radix in-register DFTs)
+             (2, (96, 200), "periodic"), (2, (200, 96), "dirichlet"), (2, (384, 96), "neumann"),
+             (2, (96, 384), "dirichlet"), (3, (96, 200, 64), "neumann"), (3, (200, 64, 384), "periodic")]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -116,7 +119,10 @@ def test_forward_transform_register_engine(dim, N, bc, dtype, S):
                                            (2, (64, 64), "neumann", "fhn"),
                                            (2, (256, 128), "neumann", "gierer_meinhardt"),
                                            (3, (64, 64, 64), "dirichlet", "schnakenberg"),
-                                           (3, (64, 64, 64), "neumann", "fhn")])
+                                           (3, (64, 64, 64), "neumann", "fhn"),
+                                           (2, (96, 200), "periodic", "gierer_meinhardt"),
+                                           (2, (384, 96), "dirichlet", "gray_scott"),
+                                           (2, (200, 384), "neumann", "schnakenberg")])
 def test_register_engine_steps_match_oracle_and_generic_engine(dim, N, bc, kind, monkeypatch):
     cfg = _cfg(dim, N, bc, kind=kind, dt=0.02)
     lo, hi = (0.0, 1.0) if kind in ("fhn", "gray_scott") else (-0.05, 0.05)
