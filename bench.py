@@ -44,7 +44,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=20,
+                    help="steps timed on the FP64 path of the same workload (0: skip FP64)")
+    ap.add_argument("--err-steps", type=int, default=500,
+                    help="steps after which FP32 is compared with FP64 on the GPU (the workload's whole run)")
+    ap.add_argument("--repeats", type=int, default=7,
+                    help="timed regions of --steps steps each; the line reports their median")
+    ap.add_argument("--gs-steps", type=int, default=200,
+                    help="steps timed on the 2D Gray-Scott 1024^2 workload, FP32 and FP64 (0: skip)")
+    ap.add_argument("--gs-err-steps", type=int, default=2000,
+                    help="steps after which the Gray-Scott FP32 path is compared with FP64 (its whole run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batched-steps", type=int, default=20)
@@ -259,21 +268,29 @@ def main():
 
     clocks = Clocks(local) if rank == 0 else None
     time.sleep(0.3 if clocks else 0.0)
-    barrier()
-    torch.cuda.synchronize()
+    # R timed regions of exactly K steps each (barrier + synchronize on both sides of every region, CUDA
+    # events on the solver's stream, max over ranks); the line reports the median region
+    regions = []
     if clocks:
         clocks.mark()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    solver.advance(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms = e0.elapsed_time(e1)
+    for _ in range(max(1, args.repeats)):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.advance(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        regions.append(max_over_ranks(e0.elapsed_time(e1)))
     clk = clocks.stop() if clocks else None
-    ms = max_over_ranks(ms)
+    ms = statistics.median(regions)
     value = dof * args.steps * world / (ms * 1e-3)
+    repeats = {"regions": len(regions), "steps_per_region": args.steps, "ms_per_step_median": ms / args.steps,
+               "ms_per_step_min": min(regions) / args.steps, "ms_per_step_max": max(regions) / args.steps,
+               "value_min": dof * args.steps * world / (max(regions) * 1e-3),
+               "value_max": dof * args.steps * world / (min(regions) * 1e-3)}
 
     # per-launch profile of the same step (events on the launching stream)
     prof = {}
@@ -301,8 +318,9 @@ def main():
                  "achieved_gbs": model_bytes / (ms * 1e-3 / args.steps) / 1e9,
                  "frac_of_" + peak_kind: model_bytes / (ms * 1e-3 / args.steps) / 1e9 / peak}
 
-    # FP64 path on the same workload, and the FP32-vs-FP64 error after the same steps
+    # FP64 path on the same workload, and the FP32-vs-FP64 error after the workload's whole run
     extra = {}
+    ref = None
     if rank == 0 and args.dtype == "f32" and args.fp64_steps > 0:
         s64 = sf.Solver(cfg, dtype="f64")
         s64.load(u0_dev.double(), 0.0)
@@ -315,12 +333,14 @@ def main():
         a1.record(s64.stream)
         torch.cuda.synchronize()
         ms64 = a0.elapsed_time(a1)
-        ref = s64.run(u0_dev.double(), nsteps=args.fp64_steps)
-        got = solver.run(u0_dev, nsteps=args.fp64_steps).double()
-        err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
         extra["fp64"] = {"value": dof * args.fp64_steps / (ms64 * 1e-3), "unit": "DOF-steps/s",
                          "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
-        extra["fp32_vs_fp64_rel_l2"] = {"value": err, "steps": args.fp64_steps}
+        if args.err_steps > 0:
+            ref = s64.run(u0_dev.double(), nsteps=args.err_steps)
+            got = solver.run(u0_dev, nsteps=args.err_steps).double()
+            err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+            extra["fp32_vs_fp64_rel_l2"] = {"value": err, "steps": args.err_steps,
+                                            "whole_run": args.err_steps == cfg["nsteps"]}
         del s64
         torch.cuda.empty_cache()
 
@@ -339,8 +359,10 @@ def main():
             r1.record(sr.stream)
             torch.cuda.synchronize()
             msr = r0.elapsed_time(r1)
-            gotr = sr.run(u0_dev, nsteps=args.fp64_steps).double()
-            errr = float(torch.linalg.vector_norm(gotr - ref) / torch.linalg.vector_norm(ref))
+            errr = None
+            if ref is not None:
+                gotr = sr.run(u0_dev, nsteps=args.err_steps).double()
+                errr = float(torch.linalg.vector_norm(gotr - ref) / torch.linalg.vector_norm(ref))
             shared = len(cfg["alpha"]) == 2 and cfg["alpha"][0] == cfg["alpha"][1]
             lw = 0.5 if shared else 1.0            # words of L per unknown, per slow-axis pass
             coef_words = {2: 2, 3: 2, 4: 2, 5: 4}  # stored coefficient words per pass kind
@@ -352,10 +374,11 @@ def main():
                 "ms_per_step": msr / args.rational_steps, "steps": args.rational_steps,
                 "model_words_per_dof_step": rwords,
                 "frac_of_" + peak_kind: rbytes / (msr * 1e-3 / args.rational_steps) / 1e9 / peak,
-                "fp32_vs_fp64_rel_l2": {"value": errr, "steps": args.fp64_steps},
+                "fp32_vs_fp64_rel_l2": {"value": errr, "steps": args.err_steps},
                 "shared_l_plane": shared}
             del sr
             torch.cuda.empty_cache()
+    ref = None
 
     # the batched workload: 256 Gierer-Meinhardt instances, one persistent launch per pass; with several
     # ranks each takes whole instances (no data-path collective) and the slowest rank sets the time
@@ -412,6 +435,48 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, args.cpu_seconds)
+
+    # the 2D Gray-Scott workload (1024^2 periodic, FP32 and FP64): throughput, its 38-word pass model against
+    # the HBM peak (the FP32 working set, about 0.1 GB, may stay in the 126 MB L2: context, not a gate), and the
+    # FP32-vs-FP64 error after its whole 2000-step run
+    if rank == 0 and args.gs_steps > 0:
+        gcfg = W.config("gs1024")
+        gu0 = torch.as_tensor(np.stack(W.initial_fields(gcfg)))
+        extra["gs1024"] = {"workload": "2D fractional Gray-Scott, periodic (Hartley), N=1024 (1024^2), alpha=1.7, "
+                                       "kappa=(2e-5,1e-5), F=0.04, K=0.06, dt=1", "steps": args.gs_steps}
+        finals = {}
+        try:
+            for dt in ("f32", "f64"):
+                sg = sf.Solver(gcfg, dtype=dt)
+                sg.load(gu0.cuda(), 0.0)
+                sg.advance(3)
+                torch.cuda.synchronize()
+                g0 = torch.cuda.Event(enable_timing=True)
+                g1 = torch.cuda.Event(enable_timing=True)
+                g0.record(sg.stream)
+                sg.advance(args.gs_steps)
+                g1.record(sg.stream)
+                torch.cuda.synchronize()
+                msg = g0.elapsed_time(g1) / args.gs_steps
+                es = 4 if dt == "f32" else 8
+                words = sum(WORDS[k] for k, _ in sg.profile_step())   # pass kinds of one step
+                extra["gs1024"][dt] = {"value": sg.dof / (msg * 1e-3), "unit": "DOF-steps/s", "ms_per_step": msg,
+                                       "model_words_per_dof_step": words,
+                                       "model_frac_of_" + peak_kind: words * sg.dof * es / (msg * 1e-3) / 1e9 / peak,
+                                       "gpu_launches_per_step": sg.kernels_per_step}
+                if args.gs_err_steps > 0:
+                    finals[dt] = sg.run(gu0.cuda(), nsteps=args.gs_err_steps).double()
+                del sg
+                torch.cuda.empty_cache()
+            if len(finals) == 2:
+                extra["gs1024"]["fp32_vs_fp64_rel_l2"] = {
+                    "value": float(torch.linalg.vector_norm(finals["f32"] - finals["f64"]) /
+                                   torch.linalg.vector_norm(finals["f64"])),
+                    "steps": args.gs_err_steps, "whole_run": args.gs_err_steps == gcfg["nsteps"]}
+        except Exception as exc:   # keep the headline line whatever happens here
+            extra["gs1024"]["error"] = "%s: %s" % (type(exc).__name__, exc)
+        finals = None
+        torch.cuda.empty_cache()
 
     # the 2D FitzHugh-Nagumo workload (65^2 Neumann nodes, its 200 steps), FP64 and FP32: a small grid whose
     # step is bound by launch latency rather than HBM; reported for completeness, errors kept in the record
@@ -479,7 +544,7 @@ def main():
                                  "%.2f GB > 126 MB)" % (solver.info.workspace_bytes / 1e9),
                            "timed": "sfrd_advance (captured CUDA graph), one ETDRK4-P13 step per bench step"},
                 "gpu_launches": solver.kernels_per_step * args.steps,
-                "roofline": roof, "step_roofline": step_roof, "kernels": per_kind,
+                "roofline": roof, "step_roofline": step_roof, "kernels": per_kind, "repeats": repeats,
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         line.update(extra)
         print(json.dumps(line), flush=True)

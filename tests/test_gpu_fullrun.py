@@ -109,9 +109,11 @@ def test_gierer_meinhardt_instance_full_run_against_stored_oracle(name):
     assert int(g["nsteps"]) == cfg["nsteps"] == 400 and tuple(g["N"]) == tuple(cfg["N"])
     u0 = W.initial_fields(cfg)
     g64 = _np(sf.Solver(cfg, dtype="f64").run(u0, nsteps=cfg["nsteps"]))
-    assert _rel_max_sampled(g64, g) < TOL64
     g32 = _np(sf.Solver(cfg, dtype="f32").run(u0, nsteps=cfg["nsteps"]))
-    assert _rel_l2_sampled(g32, g) < TOL32
+    e64, e32 = _rel_max_sampled(g64, g), _rel_l2_sampled(g32, g)
+    print("%s N=%d %s: FP64 rel max %.2e, FP32 rel L2 %.2e after 400 steps" % (name, cfg["N"][0], cfg["bc"], e64, e32))
+    assert e64 < TOL64
+    assert e32 < TOL32
 
 
 def test_batched_workload_full_run_against_stored_oracle():
