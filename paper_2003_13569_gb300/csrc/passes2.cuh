@@ -541,44 +541,27 @@ __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) x2_kerne
 }
 
 // ---- launch --------------------------------------------------------------------------
+//
+// The kernels of a length fall into four families, each with its own launch and set-up function, so
+// that a translation unit can instantiate one family: the long FP32 lengths compile as several objects
+// in parallel.  PLAIN: the column passes of every mode on the default layouts; PAIR (FP32): the stage
+// passes on element pairs, stored and rational coefficients; RAT (FP32): the rational-coefficient stage
+// passes on the default layouts; X: the contiguous-axis pass.
+
+template <typename T>
+cudaError_t set_smem_attrs(void (*k)(const T), int bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
+constexpr bool is_stage_mode(int mode) {
+    return mode == MODE_TA || mode == MODE_TB || mode == MODE_TC || mode == MODE_TD;
+}
 
 template <typename T, int N, int BCT>
-cudaError_t col2_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
-    const size_t smem = TileOf<T, N>::E::smem_bytes();
+cudaError_t col2_plain_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
     void (*k)(const ColArgs<T>) = nullptr;
-    if constexpr (sizeof(T) == 4) {
-        if (a.cstride == 2 && a.in_sp > 0) {   // slow-axis passes on element pairs
-            if (a.CL) {
-                switch (mode) {
-                    case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, true, true>; break;
-                    case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, true, true>; break;
-                    case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, true, true>; break;
-                    case MODE_TD: k = col2_kernel<T, N, MODE_TD, BCT, true, true>; break;
-                    default: break;
-                }
-            } else {
-                switch (mode) {
-                    case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, false, true>; break;
-                    case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, false, true>; break;
-                    case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, false, true>; break;
-                    case MODE_TD: k = col2_kernel<T, N, MODE_TD, BCT, false, true>; break;
-                    default: break;
-                }
-            }
-        } else if (a.CL) {   // rational-coefficient mode
-            switch (mode) {
-                case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, true>; break;
-                case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, true>; break;
-                case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, true>; break;
-                case MODE_TD: k = col2_kernel<T, N, MODE_TD, BCT, true>; break;
-                default: break;
-            }
-        }
-    }
-    if (k) {
-        k<<<grid, kThreads, smem, s>>>(a);
-        return cudaGetLastError();
-    }
     switch (mode) {
         case MODE_PLAIN: k = col2_kernel<T, N, MODE_PLAIN, BCT>; break;
         case MODE_T0: k = col2_kernel<T, N, MODE_T0, BCT>; break;
@@ -587,8 +570,97 @@ cudaError_t col2_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_
         case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT>; break;
         default: k = col2_kernel<T, N, MODE_TD, BCT>; break;
     }
-    k<<<grid, kThreads, smem, s>>>(a);
+    k<<<grid, kThreads, TileOf<T, N>::E::smem_bytes(), s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int N, int BCT>
+cudaError_t col2_plain_prepare_bc() {
+    void (*ks[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_PLAIN, BCT>, col2_kernel<T, N, MODE_T0, BCT>,
+                                      col2_kernel<T, N, MODE_TA, BCT>,    col2_kernel<T, N, MODE_TB, BCT>,
+                                      col2_kernel<T, N, MODE_TC, BCT>,    col2_kernel<T, N, MODE_TD, BCT>};
+    for (auto k : ks) {
+        const cudaError_t e = set_smem_attrs(k, kMaxDynSmem2);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Stage passes on element pairs (FP32 only); a.CL selects the rational-coefficient form.
+template <typename T, int N, int BCT>
+cudaError_t col2_pair_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        void (*k)(const ColArgs<T>) = nullptr;
+        if (a.CL) {
+            switch (mode) {
+                case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, true, true>; break;
+                case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, true, true>; break;
+                case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, true, true>; break;
+                default: k = col2_kernel<T, N, MODE_TD, BCT, true, true>; break;
+            }
+        } else {
+            switch (mode) {
+                case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, false, true>; break;
+                case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, false, true>; break;
+                case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, false, true>; break;
+                default: k = col2_kernel<T, N, MODE_TD, BCT, false, true>; break;
+            }
+        }
+        k<<<grid, kThreads, TileOf<T, N>::E::smem_bytes(), s>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int N, int BCT>
+cudaError_t col2_pair_prepare_bc() {
+    if constexpr (sizeof(T) == 4) {
+        void (*ks[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_TA, BCT, false, true>,
+                                          col2_kernel<T, N, MODE_TB, BCT, false, true>,
+                                          col2_kernel<T, N, MODE_TC, BCT, false, true>,
+                                          col2_kernel<T, N, MODE_TD, BCT, false, true>,
+                                          col2_kernel<T, N, MODE_TA, BCT, true, true>,
+                                          col2_kernel<T, N, MODE_TB, BCT, true, true>,
+                                          col2_kernel<T, N, MODE_TC, BCT, true, true>,
+                                          col2_kernel<T, N, MODE_TD, BCT, true, true>};
+        for (auto k : ks) {
+            const cudaError_t e = set_smem_attrs(k, kMaxDynSmem2);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+// Rational-coefficient stage passes on the default layouts (FP32 only).
+template <typename T, int N, int BCT>
+cudaError_t col2_rat_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        void (*k)(const ColArgs<T>) = nullptr;
+        switch (mode) {
+            case MODE_TA: k = col2_kernel<T, N, MODE_TA, BCT, true>; break;
+            case MODE_TB: k = col2_kernel<T, N, MODE_TB, BCT, true>; break;
+            case MODE_TC: k = col2_kernel<T, N, MODE_TC, BCT, true>; break;
+            default: k = col2_kernel<T, N, MODE_TD, BCT, true>; break;
+        }
+        k<<<grid, kThreads, TileOf<T, N>::E::smem_bytes(), s>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int N, int BCT>
+cudaError_t col2_rat_prepare_bc() {
+    if constexpr (sizeof(T) == 4) {
+        void (*ks[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_TA, BCT, true>, col2_kernel<T, N, MODE_TB, BCT, true>,
+                                          col2_kernel<T, N, MODE_TC, BCT, true>, col2_kernel<T, N, MODE_TD, BCT, true>};
+        for (auto k : ks) {
+            const cudaError_t e = set_smem_attrs(k, kMaxDynSmem2);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
 }
 
 template <typename T, int N, int BCT>
@@ -601,46 +673,33 @@ cudaError_t x2_launch_bc(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s)
 }
 
 template <typename T, int N, int BCT>
-cudaError_t prepare2_bc() {
-    const int m = kMaxDynSmem2;
-    void (*ks[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_PLAIN, BCT>, col2_kernel<T, N, MODE_T0, BCT>,
-                                      col2_kernel<T, N, MODE_TA, BCT>,    col2_kernel<T, N, MODE_TB, BCT>,
-                                      col2_kernel<T, N, MODE_TC, BCT>,    col2_kernel<T, N, MODE_TD, BCT>};
-    for (auto k : ks) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e != cudaSuccess) return e;
-    }
-    if constexpr (sizeof(T) == 4) {
-        void (*kr[])(const ColArgs<T>) = {col2_kernel<T, N, MODE_TA, BCT, true>, col2_kernel<T, N, MODE_TB, BCT, true>,
-                                          col2_kernel<T, N, MODE_TC, BCT, true>, col2_kernel<T, N, MODE_TD, BCT, true>,
-                                          col2_kernel<T, N, MODE_TA, BCT, false, true>,
-                                          col2_kernel<T, N, MODE_TB, BCT, false, true>,
-                                          col2_kernel<T, N, MODE_TC, BCT, false, true>,
-                                          col2_kernel<T, N, MODE_TD, BCT, false, true>,
-                                          col2_kernel<T, N, MODE_TA, BCT, true, true>,
-                                          col2_kernel<T, N, MODE_TB, BCT, true, true>,
-                                          col2_kernel<T, N, MODE_TC, BCT, true, true>,
-                                          col2_kernel<T, N, MODE_TD, BCT, true, true>};
-        for (auto k : kr) {
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-            if (e != cudaSuccess) return e;
-        }
-    }
+cudaError_t x2_prepare_bc() {
     void (*xs[])(const XArgs<T>) = {x2_kernel<T, N, MODE_PLAIN, BCT>, x2_kernel<T, N, MODE_REACT, BCT>};
     for (auto k : xs) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        const cudaError_t e = set_smem_attrs(k, kMaxDynSmem2);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// Per-boundary-condition variants (translation units of their own for the specialised lengths).
-template <typename T, int N, int BCT> cudaError_t col2_launch_bc(const ColArgs<T>&, int, dim3, cudaStream_t);
-template <typename T, int N, int BCT> cudaError_t x2_launch_bc(const XArgs<T>&, int, dim3, cudaStream_t);
-template <typename T, int N, int BCT> cudaError_t prepare2_bc();
+// Column-pass dispatch to the family (instantiates no kernel itself).
+template <typename T, int N, int BCT>
+cudaError_t col2_launch_bc(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (is_stage_mode(mode) && a.cstride == 2 && a.in_sp > 0) return col2_pair_launch_bc<T, N, BCT>(a, mode, grid, s);
+        if (is_stage_mode(mode) && a.CL) return col2_rat_launch_bc<T, N, BCT>(a, mode, grid, s);
+    }
+    return col2_plain_launch_bc<T, N, BCT>(a, mode, grid, s);
+}
+
+template <typename T, int N, int BCT>
+cudaError_t prepare2_bc() {
+    cudaError_t e = col2_plain_prepare_bc<T, N, BCT>();
+    if (e == cudaSuccess) e = col2_pair_prepare_bc<T, N, BCT>();
+    if (e == cudaSuccess) e = col2_rat_prepare_bc<T, N, BCT>();
+    if (e == cudaSuccess) e = x2_prepare_bc<T, N, BCT>();
+    return e;
+}
 
 template <typename T, int N>
 cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
@@ -677,16 +736,58 @@ cudaError_t prepare2() {
     return prepare2_bc<T, N, -1>();
 }
 
+// Explicit instantiation.  SFRD_V2_INSTANTIATE emits a whole length in one object; a length split over
+// several objects emits SFRD_V2_DISPATCH once and each family macro in an object of its own.  The
+// dispatchers are only declared where they are not emitted.
+#define SFRD_V2_DISPATCH_BC(T, N, BCT)                                                             \
+    template cudaError_t col2_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t);   \
+    template cudaError_t prepare2_bc<T, N, BCT>();
+
+#define SFRD_V2_DISPATCH(T, N)                                                                     \
+    template cudaError_t col2_launch<T, N>(const ColArgs<T>&, int, dim3, cudaStream_t);           \
+    template cudaError_t x2_launch<T, N>(const XArgs<T>&, int, dim3, cudaStream_t);               \
+    template cudaError_t prepare2<T, N>();                                                        \
+    SFRD_V2_DISPATCH_BC(T, N, -1)
+
+#define SFRD_V2_PLAIN(T, N, BCT)                                                                   \
+    template cudaError_t col2_plain_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t); \
+    template cudaError_t col2_plain_prepare_bc<T, N, BCT>();
+
+#define SFRD_V2_PAIR(T, N, BCT)                                                                    \
+    template cudaError_t col2_pair_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t); \
+    template cudaError_t col2_pair_prepare_bc<T, N, BCT>();
+
+#define SFRD_V2_RAT(T, N, BCT)                                                                     \
+    template cudaError_t col2_rat_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t); \
+    template cudaError_t col2_rat_prepare_bc<T, N, BCT>();
+
+#define SFRD_V2_X(T, N, BCT)                                                                       \
+    template cudaError_t x2_launch_bc<T, N, BCT>(const XArgs<T>&, int, dim3, cudaStream_t);       \
+    template cudaError_t x2_prepare_bc<T, N, BCT>();
+
+// Declares the families of a split length as instantiated elsewhere (keeps the dispatch object free of kernels).
+#define SFRD_V2_EXTERN_FAMILIES(T, N, BCT)                                                                  \
+    extern template cudaError_t col2_plain_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t); \
+    extern template cudaError_t col2_plain_prepare_bc<T, N, BCT>();                                         \
+    extern template cudaError_t col2_pair_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t);  \
+    extern template cudaError_t col2_pair_prepare_bc<T, N, BCT>();                                          \
+    extern template cudaError_t col2_rat_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t);   \
+    extern template cudaError_t col2_rat_prepare_bc<T, N, BCT>();                                           \
+    extern template cudaError_t x2_launch_bc<T, N, BCT>(const XArgs<T>&, int, dim3, cudaStream_t);          \
+    extern template cudaError_t x2_prepare_bc<T, N, BCT>();
+
+#define SFRD_V2_INSTANTIATE_BC(T, N, BCT)                                                          \
+    SFRD_V2_DISPATCH_BC(T, N, BCT)                                                                 \
+    SFRD_V2_PLAIN(T, N, BCT)                                                                       \
+    SFRD_V2_PAIR(T, N, BCT)                                                                        \
+    SFRD_V2_RAT(T, N, BCT)                                                                         \
+    SFRD_V2_X(T, N, BCT)
+
 #define SFRD_V2_INSTANTIATE(T, N)                                                                  \
     template cudaError_t col2_launch<T, N>(const ColArgs<T>&, int, dim3, cudaStream_t);           \
     template cudaError_t x2_launch<T, N>(const XArgs<T>&, int, dim3, cudaStream_t);               \
     template cudaError_t prepare2<T, N>();                                                        \
     SFRD_V2_INSTANTIATE_BC(T, N, -1)
-
-#define SFRD_V2_INSTANTIATE_BC(T, N, BCT)                                                          \
-    template cudaError_t col2_launch_bc<T, N, BCT>(const ColArgs<T>&, int, dim3, cudaStream_t);   \
-    template cudaError_t x2_launch_bc<T, N, BCT>(const XArgs<T>&, int, dim3, cudaStream_t);       \
-    template cudaError_t prepare2_bc<T, N, BCT>();
 
 }  // namespace v2
 }  // namespace sfrd

@@ -1,9 +1,22 @@
-// Register-FFT passes, F32, axis length 1024.
+// Register-FFT passes, FP32, axis length 1024, compiled as five objects (SFRD_TU_PART 0-4): dispatch and
+// plain column passes, element-pair stage passes, rational-coefficient stage passes, contiguous-axis
+// pass, adjoint passes.
 #include "adjoint.cuh"
 
 namespace sfrd {
 namespace v2 {
-SFRD_V2_INSTANTIATE(float, 1024)
+#if SFRD_TU_PART == 0
+SFRD_V2_EXTERN_FAMILIES(float, 1024, -1)
+SFRD_V2_DISPATCH(float, 1024)
+SFRD_V2_PLAIN(float, 1024, -1)
+#elif SFRD_TU_PART == 1
+SFRD_V2_PAIR(float, 1024, -1)
+#elif SFRD_TU_PART == 2
+SFRD_V2_RAT(float, 1024, -1)
+#elif SFRD_TU_PART == 3
+SFRD_V2_X(float, 1024, -1)
+#elif SFRD_TU_PART == 4
 SFRD_ADJ_INSTANTIATE(float, 1024)
+#endif
 }  // namespace v2
 }  // namespace sfrd

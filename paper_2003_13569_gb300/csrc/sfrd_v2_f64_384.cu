@@ -1,9 +1,22 @@
-// Register-FFT passes, F64, axis length 384.
+// Register-FFT passes, FP64, axis length 384, compiled as five objects (SFRD_TU_PART 0-4): dispatch and
+// plain column passes, element-pair stage passes, rational-coefficient stage passes, contiguous-axis
+// pass, adjoint passes.
 #include "adjoint.cuh"
 
 namespace sfrd {
 namespace v2 {
-SFRD_V2_INSTANTIATE(double, 384)
+#if SFRD_TU_PART == 0
+SFRD_V2_EXTERN_FAMILIES(double, 384, -1)
+SFRD_V2_DISPATCH(double, 384)
+SFRD_V2_PLAIN(double, 384, -1)
+#elif SFRD_TU_PART == 1
+SFRD_V2_PAIR(double, 384, -1)
+#elif SFRD_TU_PART == 2
+SFRD_V2_RAT(double, 384, -1)
+#elif SFRD_TU_PART == 3
+SFRD_V2_X(double, 384, -1)
+#elif SFRD_TU_PART == 4
 SFRD_ADJ_INSTANTIATE(double, 384)
+#endif
 }  // namespace v2
 }  // namespace sfrd
