@@ -527,10 +527,33 @@ def main():
             extra["adjoint"] = {"value": sa.dof * n / ((fwd + rev) * 1e-3),
                                 "unit": "DOF-steps/s (checkpointed forward + reverse sweep)",
                                 "forward_ms": fwd, "reverse_ms": rev, "steps": n, "checkpoint_every": K,
-                                "dtype": "f64", "dL_dalpha": grads[1],
+                                "dtype": "f64", "dL_dalpha": grads[1], "dL_dkappa": grads[2],
+                                "dL_dparams": list(grads[3][:1]),
                                 "workload": "2D fractional FitzHugh-Nagumo, Neumann, N=256 (257^2 nodes), "
                                             "loss 0.5||u_T - target||^2"}
             del sa
+            # the same forward run and reverse sweep in FP32 (FP64 coefficients), its errors against FP64
+            s32 = sf.Solver(acfg, dtype="f32")
+            uT32 = s32.run_checkpointed(u0a, 0.0, n, K)
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            uT32 = s32.run_checkpointed(u0a, 0.0, n, K)
+            b0.record(s32.stream)
+            g32 = s32.adjoint(uT32 - tgt.float(), 0.0, n, K)
+            b1.record(s32.stream)
+            torch.cuda.synchronize()
+
+            def rel(a, b):
+                return abs(float(a) - float(b)) / max(abs(float(b)), 1e-300)
+
+            d64, d32 = grads[0].double(), g32[0].double()
+            extra["adjoint"]["f32"] = {
+                "reverse_ms": b0.elapsed_time(b1),
+                "uT_rel_l2_vs_f64": float((uT32.double() - uT).norm() / uT.norm()),
+                "dL_du0_rel_l2_vs_f64": float((d32 - d64).norm() / d64.norm()),
+                "dL_dalpha_rel_vs_f64": rel(g32[1][0], grads[1][0]),
+                "dL_dkappa_rel_vs_f64": rel(g32[2][0], grads[2][0]),
+                "dL_dparams_rel_vs_f64": rel(g32[3][0], grads[3][0])}
+            del s32
         except Exception as exc:
             extra["adjoint"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
 

@@ -163,8 +163,9 @@ int sfrd_set_coefficients(sfrd_plan_t plan, int32_t mode);
  * FP64 at bind time: Taylor series of the phi-functions for L < 1, closed forms
  * otherwise); a single eigenmode then decays by exactly exp(-kappa
  * Lambda^{alpha/2} t) under zero reaction.  Call before sfrd_bind.  The
- * Cox-Matthews scheme uses stored coefficient arrays (not SFRD_COEF_RATIONAL)
- * and has no adjoint (sfrd_adjoint* return SFRD_EUNSUPPORTED).
+ * Cox-Matthews scheme uses stored coefficient arrays (not SFRD_COEF_RATIONAL);
+ * its adjoint runs the same reverse sweep over those arrays, with the kappa and
+ * alpha gradients through dC/dL of the exact-exponential coefficients.
  * Errors: SFRD_EINVAL (scheme), SFRD_EUNSUPPORTED, SFRD_ESTATE (already bound). */
 #define SFRD_SCHEME_P13           0
 #define SFRD_SCHEME_COX_MATTHEWS  1
@@ -289,7 +290,8 @@ int sfrd_profile_step(sfrd_plan_t plan, int32_t cap, float* ms, int32_t* kind);
  * [64, 1024], or 96, 200 or 384 (SFRD_EUNSUPPORTED otherwise).  The adjoint is
  * the exact transpose of the library's own FP arithmetic path (transposed transforms, the same
  * coefficient arrays, the reaction Jacobian transposed), i.e. the gradient of
- * the discrete map u0 -> u(t0 + nsteps tau) of Eq. ETDRK4P13.
+ * the discrete map u0 -> u(t0 + nsteps tau) of Eq. ETDRK4P13 (or of the
+ * Cox-Matthews step of sfrd_set_scheme, whose coefficient arrays it then uses).
  *
  * Memory: a caller-owned device buffer of sfrd_adjoint_workspace_bytes(nsteps,
  * ckpt_every) bytes (256-byte aligned) holds one spectral checkpoint every

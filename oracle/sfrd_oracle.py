@@ -524,6 +524,37 @@ def coefficient_derivatives(L, tau: float) -> dict:
     }
 
 
+def cox_matthews_derivatives(L, tau: float, npts: int = 64) -> dict:
+    """d(coefficient)/dL for the six Cox-Matthews arrays of cox_matthews_coefficients.
+
+    Each coefficient is an entire function c(z) of z = -L (the forms' poles at 0 are removable), so
+    its derivative is the Cauchy integral dc/dz = (1/2 pi i) [contour integral of] c(w) / (w - z)^2 dw, i.e. the mean
+    of c(w) / (w - z) over a circle around z.  The radius is |z| + 1 for |z| < 2 (the circle keeps a
+    distance of 1 from the origin, where the forms cancel) and 1 otherwise (every point then has
+    |w| >= 1 and Re w <= -1: no cancellation beyond the forms' own, no overflow).  dc/dL = -dc/dz."""
+    L = np.asarray(L, dtype=np.float64)
+    z = -L
+    unit = np.exp(2j * np.pi * (np.arange(npts) + 0.5) / npts)
+
+    def forms(Z):
+        eZ = np.exp(Z)
+        Z3 = Z ** 3
+        return {"R13": eZ,
+                "Q13": np.exp(Z / 2),
+                "phi": tau / 2 * (np.exp(Z / 2) - 1.0) / (Z / 2),
+                "phi1": tau * (-4.0 - Z + eZ * (4.0 - 3.0 * Z + Z ** 2)) / Z3,
+                "phi2": 2.0 * tau * (2.0 + Z + eZ * (Z - 2.0)) / Z3,
+                "phi3": tau * (-4.0 - 3.0 * Z - Z ** 2 + eZ * (4.0 - Z)) / Z3}
+
+    r = np.where(np.abs(z) < 2.0, np.abs(z) + 1.0, 1.0)
+    pts = z[..., None] + r[..., None] * unit
+    vals = forms(pts)
+    return {k: -(v / (pts - z[..., None])).mean(axis=-1).real for k, v in vals.items()}
+
+
+COEFFICIENT_DERIVATIVES = {"p13": coefficient_derivatives, "cox_matthews": cox_matthews_derivatives}
+
+
 def adjoint_run(solver: ETDRK4P13, u0: list, t0: float, nsteps: int, dldu_T: list,
                 dparams: Callable | None = None) -> dict:
     """Gradient of l(u_M) through M steps: dl/du0, dl/dalpha_s, dl/dkappa_s, dl/dtheta.
@@ -532,8 +563,6 @@ def adjoint_run(solver: ETDRK4P13, u0: list, t0: float, nsteps: int, dldu_T: lis
     dl/dkappa_s = sum dl/dC * dC/dL * tau Lambda^{alpha_s/2};
     dl/dalpha_s = sum dl/dC * dC/dL * kappa_s tau Lambda^{alpha_s/2} ln(Lambda)/2 (0 where Lambda = 0).
     """
-    if solver.scheme != "p13":
-        raise NotImplementedError("the adjoint differentiates the Pade-(1,3) coefficients")
     prob = solver.prob
     S = prob.nspecies
     states = [[np.array(x, dtype=np.float64) for x in u0]]
@@ -549,7 +578,7 @@ def adjoint_run(solver: ETDRK4P13, u0: list, t0: float, nsteps: int, dldu_T: lis
     logLam = np.where(Lam > 0, np.log(np.where(Lam > 0, Lam, 1.0)), 0.0)
     dalpha, dkappa = [], []
     for s in range(S):
-        dC = coefficient_derivatives(solver.L[s], prob.tau)
+        dC = COEFFICIENT_DERIVATIVES[solver.scheme](solver.L[s], prob.tau)
         dLdC = sum((dcoef[s].get(n, 0.0) * dC[n]).sum() for n in dC) if dcoef[s] else 0.0
         g_L = sum(dcoef[s].get(n, 0.0) * dC[n] for n in dC) if dcoef[s] else 0.0
         Lf = solver.sp.Lambda_frac(prob.alpha[s])

@@ -73,4 +73,35 @@ __device__ inline void cm_coefficients(double L, double tau, double& R, double& 
     }
 }
 
+// psi_0..psi_4 at z <= 0: Taylor series for |z| < 1, else psi_0 = e^z and the recurrence
+// psi_{k+1} = (psi_k - 1/k!) / z (each step divides by |z| >= 1: absolute errors do not grow).
+__device__ inline void cm_psi(double z, double* ps) {
+    if (z > -1.0) {
+#pragma unroll
+        for (int k = 0; k <= 4; ++k) ps[k] = cm_series(z, k);
+    } else {
+        ps[0] = exp(z);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ps[k + 1] = (ps[k] - kCmInvFact[k]) / z;
+    }
+}
+
+// dC/dL of the Cox-Matthews coefficients, order R, Q, phi, phi1, phi2, phi3 (the slots of
+// R13, Q13, phi, phi1, phi2, phi3).  With z = -L (dz/dL = -1) and psi_k' = psi_k - k psi_{k+1}
+// (term-by-term from the series):
+//   d e^z = e^z;  d[(tau/2) psi1(z/2)]/dz = (tau/4)(psi1 - psi2)(z/2);
+//   phi1' = tau (psi1 - 4 psi2 + 10 psi3 - 12 psi4),  phi2' = 2 tau (psi2 - 4 psi3 + 6 psi4),
+//   phi3' = tau (-psi2 + 6 psi3 - 12 psi4)   (derivatives in z).
+__device__ inline void cm_dcoef_dL(double L, double tau, double* d) {
+    double ps[5], pw[5];
+    cm_psi(-L, ps);
+    cm_psi(-0.5 * L, pw);
+    d[0] = -ps[0];
+    d[1] = -0.5 * pw[0];
+    d[2] = -0.25 * tau * (pw[1] - pw[2]);
+    d[3] = -tau * (ps[1] - 4.0 * ps[2] + 10.0 * ps[3] - 12.0 * ps[4]);
+    d[4] = -2.0 * tau * (ps[2] - 4.0 * ps[3] + 6.0 * ps[4]);
+    d[5] = -tau * (-ps[2] + 6.0 * ps[3] - 12.0 * ps[4]);
+}
+
 }  // namespace sfrd

@@ -19,6 +19,7 @@
 // the inverse is F / C.  All passes run in place on the work array.
 #pragma once
 
+#include "adjgrad.cuh"
 #include "coef.cuh"
 #include "engine.cuh"
 #include "reaction.cuh"
@@ -593,6 +594,7 @@ static ColArgs<T> col_args(const Plan& p, int d, const Arr<T>& in, const Arr<T>&
         a.kappa[k] = p.kappa[p.S == 2 ? k : 0];
     }
     a.tau = p.dt;
+    a.scheme = p.scheme;
     const int xlim = in.xlim > out.xlim ? in.xlim : out.xlim;
     grid = dim3((xlim + a.xw - 1) / a.xw, gy, pairs ? p.S : 1);
     return a;
@@ -733,9 +735,16 @@ __global__ void __launch_bounds__(kThreads) combine1d_kernel(const ColArgs<T> a,
 }
 
 template <typename T>
-static cudaError_t run_combine1d(const Plan& p, int mode, const Arr<T>& W, cudaStream_t s) {
+static cudaError_t run_combine1d(const Plan& p, int mode, const Arr<T>& W, cudaStream_t s,
+                                 const StepSave* sv = nullptr) {
     dim3 grid;
     ColArgs<T> a = col_args<T>(p, 0, W, W, 1.0, grid);
+    if (sv) {   // the stage spectra of this step go to the recomputation arrays
+        a.F1 = static_cast<T*>(sv->F[0]);
+        a.F2 = static_cast<T*>(sv->F[1]);
+        a.F3 = static_cast<T*>(sv->F[2]);
+        a.F4 = static_cast<T*>(sv->F[3]);
+    }
     const long long total = (long long)p.S * p.plane;
     const int blocks = (int)((total + kThreads - 1) / kThreads < 1024 ? (total + kThreads - 1) / kThreads : 1024);
     switch (mode) {
@@ -744,6 +753,83 @@ static cudaError_t run_combine1d(const Plan& p, int mode, const Arr<T>& W, cudaS
         case MODE_TB: combine1d_kernel<T, MODE_TB><<<blocks, kThreads, 0, s>>>(a, total, p.plane); break;
         case MODE_TC: combine1d_kernel<T, MODE_TC><<<blocks, kThreads, 0, s>>>(a, total, p.plane); break;
         default: combine1d_kernel<T, MODE_TD><<<blocks, kThreads, 0, s>>>(a, total, p.plane); break;
+    }
+    return cudaGetLastError();
+}
+
+// Reverse of the 1D stage combinations (the adjoint's slow-axis modes without the slow-axis
+// transform: in 1D the combination acts on the x spectra directly).  Element e of [S][pitch], mode
+// index kx = e mod pitch; tilde cotangents as in the multi-dimensional sweep, t = in * (1/C):
+//   ENTRY: out = phi3 Ub                               (cotangents of R13, phi1, phi2, phi3)
+//   CB:    Cb = t;  out = phi2 Ub + 2 phi Cb
+//   BA:    Bb = t;  out = phi2 Ub + phi Bb
+//   AU:    Ab = Q Cb + t;  out = phi1 Ub - phi Cb + phi Ab
+//   EXIT:  Ub <- R13 Ub + Q (Bb + Ab) + t
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) adj_combine1d_kernel(const ColArgs<T> a, long long total, long long plane,
+                                                                  int pitch) {
+    const bool neu = a.ax.bc == SFRD_BC_NEUMANN;
+    const T invC = (T)a.invC;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(e / plane);
+        const int kx = (int)(e % plane) % pitch;
+        if (kx >= a.nk[0]) continue;                      // padding: zeros in and out
+        const double w = v2::endw(kx, a.nk[0], neu);
+        const int s = a.S == 2 ? h : 0;
+        const T ub = a.Ub[e];
+        double cb[6] = {0, 0, 0, 0, 0, 0};
+        if (MODE == MODE_ADJ_ENTRY) {
+            const double wu = w * (double)ub;
+            cb[0] = wu * a.U[e];
+            cb[3] = wu * a.F1[e];
+            cb[4] = wu * ((double)a.F2[e] + a.F3[e]);
+            cb[5] = wu * a.F4[e];
+            a.out[e] = a.CR[4 * e + 3] * ub;
+        } else {
+            const T t = a.in[e] * invC;
+            const T Q = a.CQ[2 * e], ph = a.CQ[2 * e + 1];
+            if (MODE == MODE_ADJ_CB) {
+                a.Cb[e] = t;
+                cb[1] = w * (double)t * ((double)Q * a.U[e] + (double)ph * a.F1[e]);
+                cb[2] = w * (double)t * (2.0 * a.F3[e] - a.F1[e]);
+                a.out[e] = a.CR[4 * e + 2] * ub + (T)2 * ph * t;
+            } else if (MODE == MODE_ADJ_BA) {
+                a.Bb[e] = t;
+                cb[1] = w * (double)t * a.U[e];
+                cb[2] = w * (double)t * a.F2[e];
+                a.out[e] = a.CR[4 * e + 2] * ub + ph * t;
+            } else if (MODE == MODE_ADJ_AU) {
+                const T cbv = a.Cb[e];
+                const T ah = Q * cbv + t;
+                a.Ab[e] = ah;
+                cb[1] = w * (double)ah * a.U[e];
+                cb[2] = w * (double)ah * a.F1[e];
+                a.out[e] = a.CR[4 * e + 1] * ub - ph * cbv + ph * ah;
+            } else {
+                a.Ub[e] = a.CR[4 * e] * ub + Q * (a.Bb[e] + a.Ab[e]) + t;
+            }
+        }
+        if (MODE != MODE_ADJ_EXIT) v2::coef_grad(a, s, kx, 0, 0, cb, acc);
+    }
+    v2::flush_sums<4>(acc, a.grad);
+}
+
+// One reverse 1D combination: in -> out (may alias: every element is read before it is written).
+template <typename T>
+static cudaError_t run_adj_combine1d(const Plan& p, int mode, ColArgs<T> a, const T* in, T* out, cudaStream_t s) {
+    a.in = in;
+    a.out = out;
+    const long long total = (long long)p.S * p.plane;
+    const int blocks = (int)((total + kThreads - 1) / kThreads < 1024 ? (total + kThreads - 1) / kThreads : 1024);
+    const int pitch = (int)p.pitch;
+    switch (mode) {
+        case MODE_ADJ_ENTRY: adj_combine1d_kernel<T, MODE_ADJ_ENTRY><<<blocks, kThreads, 0, s>>>(a, total, p.plane, pitch); break;
+        case MODE_ADJ_CB: adj_combine1d_kernel<T, MODE_ADJ_CB><<<blocks, kThreads, 0, s>>>(a, total, p.plane, pitch); break;
+        case MODE_ADJ_BA: adj_combine1d_kernel<T, MODE_ADJ_BA><<<blocks, kThreads, 0, s>>>(a, total, p.plane, pitch); break;
+        case MODE_ADJ_AU: adj_combine1d_kernel<T, MODE_ADJ_AU><<<blocks, kThreads, 0, s>>>(a, total, p.plane, pitch); break;
+        default: adj_combine1d_kernel<T, MODE_ADJ_EXIT><<<blocks, kThreads, 0, s>>>(a, total, p.plane, pitch); break;
     }
     return cudaGetLastError();
 }
@@ -792,7 +878,7 @@ static cudaError_t step_impl(Plan& p, cudaStream_t s, cudaEvent_t* ev, int* kind
             }
             SFRD_TRY(done());
             SFRD_TRY(mark(PASS_SLOW_A + st));
-            SFRD_TRY(run_combine1d<T>(p, MODE_TA + st, W, s));
+            SFRD_TRY(run_combine1d<T>(p, MODE_TA + st, W, s, sv));
             SFRD_TRY(done());
             continue;
         }
@@ -1006,17 +1092,28 @@ cudaError_t launch_adjoint(Plan& p, double t0, int64_t nsteps, int64_t K, char* 
 
     // entry: Ub~ = T(g ./ w) / C
     SFRD_TRY(dense_weights<T>(p, dLduT, p.ws + p.off_D, true, s));
-    SFRD_TRY(run_x<T>(p, MODE_PLAIN, D, W2, p.pitch, 0.0, s));
-    if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
-    SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, W2, UB, 1.0 / C, s));
+    if (p.dim == 1) {
+        scale1d_kernel<T><<<64, kThreads, 0, s>>>(D.ptr, wsT<T>(p, p.off_W2), p.n[0], p.pitch, p.S, 1.0 / C);
+        SFRD_TRY(cudaGetLastError());
+        SFRD_TRY(run_x<T>(p, MODE_PLAIN, W2, UB, p.pitch, 0.0, s));
+    } else {
+        SFRD_TRY(run_x<T>(p, MODE_PLAIN, D, W2, p.pitch, 0.0, s));
+        if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
+        SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, W2, UB, 1.0 / C, s));
+    }
 
     const size_t per_step = 9 * L.fld;   // u^, F1..F4, u, a, b, c
     for (int64_t seg = L.nseg - 1; seg >= 0; --seg) {
         const int64_t k0 = seg * K;
         const int64_t ns = k0 + K <= nsteps ? K : nsteps - k0;
         // recompute the segment from its checkpoint, saving every step's intermediates
-        SFRD_TRY(cudaMemcpyAsync(p.ws + p.off_U, aws + L.off_ckpt + seg * L.fld, L.fld, cudaMemcpyDeviceToDevice, s));
-        SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, internal_arr<T>(p, p.off_U), W, 1.0 / C, s));
+        if (p.dim == 1) {   // W = checkpoint, then U = W, W = W / C (the load's last pass)
+            SFRD_TRY(cudaMemcpyAsync(p.ws + p.off_W, aws + L.off_ckpt + seg * L.fld, L.fld, cudaMemcpyDeviceToDevice, s));
+            SFRD_TRY(run_combine1d<T>(p, MODE_T0, W, s));
+        } else {
+            SFRD_TRY(cudaMemcpyAsync(p.ws + p.off_U, aws + L.off_ckpt + seg * L.fld, L.fld, cudaMemcpyDeviceToDevice, s));
+            SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, internal_arr<T>(p, p.off_U), W, 1.0 / C, s));
+        }
         SFRD_TRY(launch_set_clock(p, t0, s, k0));
         for (int64_t j = 0; j < ns; ++j) {
             char* st = aws + L.off_seg + j * per_step;
@@ -1045,6 +1142,11 @@ cudaError_t launch_adjoint(Plan& p, double t0, int64_t nsteps, int64_t K, char* 
             };
             auto slow_pass = [&](int mode, const Arr<T>& in) -> cudaError_t {
                 dim3 grid;
+                if (p.dim == 1) {   // the combination acts on the x spectra directly
+                    ColArgs<T> a = col_args<T>(p, 0, in, W, 1.0, grid);
+                    patch(a);
+                    return run_adj_combine1d<T>(p, mode, a, in.ptr, const_cast<T*>(W.ptr), s);
+                }
                 ColArgs<T> a = col_args<T>(p, slow, in, W, 1.0, grid);
                 patch(a);
                 return launch_col<T>(p, slow, mode, a, grid, s);
@@ -1074,9 +1176,13 @@ cudaError_t launch_adjoint(Plan& p, double t0, int64_t nsteps, int64_t K, char* 
         }
     }
     // exit: dL/du0 = w .* T(Ub~)
-    SFRD_TRY(run_x<T>(p, MODE_PLAIN, UB, W2, p.pitch, 0.0, s));
-    if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
-    SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, W2, D, 1.0, s));
+    if (p.dim == 1) {
+        SFRD_TRY(run_x<T>(p, MODE_PLAIN, UB, D, 0, 0.0, s));
+    } else {
+        SFRD_TRY(run_x<T>(p, MODE_PLAIN, UB, W2, p.pitch, 0.0, s));
+        if (p.dim == 3) SFRD_TRY(run_col<T>(p, 1, MODE_PLAIN, W2, W2, 1.0, s));
+        SFRD_TRY(run_col<T>(p, slow, MODE_PLAIN, W2, D, 1.0, s));
+    }
     return dense_weights<T>(p, p.ws + p.off_D, dLdu0, false, s);
 }
 

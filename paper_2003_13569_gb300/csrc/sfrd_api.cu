@@ -406,9 +406,7 @@ AdjLayout adj_layout(const Plan& p, int64_t nsteps, int64_t K) {
 }
 
 static bool adjoint_capable(const Plan& p) {
-    if (p.dim == 1) return false;
     if (p.coef_mode == SFRD_COEF_RATIONAL) return false;   // the adjoint differentiates the stored arrays
-    if (p.scheme != SFRD_SCHEME_P13) return false;         // ... of the Padé(1,3) scheme
     for (int d = 0; d < p.dim; ++d)
         if (!p.v2[d]) return false;
     return true;

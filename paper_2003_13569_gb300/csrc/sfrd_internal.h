@@ -97,6 +97,7 @@ struct ColArgs {
     int dim;
     int S;
     double alpha[2], kappa[2], tau;
+    int scheme;           // SFRD_SCHEME_*: which coefficients the adjoint differentiates
     // SFRD_COEF_RATIONAL: the slow-axis combinations evaluate the coefficients from L = cl_mult[h] *
     // CL[i + (h ? clB : 0)] (line h of the tile); CL == nullptr with stored coefficient arrays.  On the
     // element-pair grid (species s = blockIdx.z, both lines of species s) the L of element i of species

@@ -57,7 +57,9 @@ CASES = [((64, 64), "neumann", "fhn", 2), ((64, 128), "periodic", "gray_scott", 
          ((64, 64, 64), "dirichlet", "schnakenberg", 3),
          # register-engine lengths 3 * 2^5, 5^2 * 2^3 and 3 * 2^7
          ((96, 200), "dirichlet", "fhn", 2), ((200, 96), "periodic", "gierer_meinhardt", 2),
-         ((384, 96), "neumann", "gray_scott", 2)]
+         ((384, 96), "neumann", "gray_scott", 2),
+         # 1D plans: the reverse combinations act on the x spectra directly
+         ((128,), "neumann", "fhn", 1), ((96,), "dirichlet", "gray_scott", 1), ((256,), "periodic", "schnakenberg", 1)]
 
 
 @pytest.mark.parametrize("N,bc,kind,dim", CASES)
@@ -80,7 +82,7 @@ def test_adjoint_matches_oracle_adjoint(N, bc, kind, dim):
         assert _rel(dp[0], ref["params"]) < 1e-8
 
 
-@pytest.mark.parametrize("N,bc,kind,dim", CASES[:4] + CASES[5:6])
+@pytest.mark.parametrize("N,bc,kind,dim", CASES[:4] + CASES[5:6] + CASES[8:10])
 def test_adjoint_matches_central_differences(N, bc, kind, dim):
     cfg = _cfg(N, bc, kind, dim=dim)
     nsteps, K = 6, 4
@@ -115,6 +117,36 @@ def test_adjoint_matches_central_differences(N, bc, kind, dim):
     v = np.random.default_rng(9).standard_normal(u0.shape)
     fd = (_loss(cfg, u0 + h * v, target, nsteps) - _loss(cfg, u0 - h * v, target, nsteps)) / (2 * h)
     assert _rel(float(np.sum(du0 * v)), fd) < 1e-6
+
+
+@pytest.mark.parametrize("N,bc,kind,dim", [((64, 64), "neumann", "fhn", 2), ((96, 128), "dirichlet", "schnakenberg", 2),
+                                          ((64, 64, 64), "periodic", "gray_scott", 3)])
+def test_cox_matthews_adjoint_matches_oracle_and_central_differences(N, bc, kind, dim):
+    """The adjoint of the Cox-Matthews scheme: the same reverse sweep over its coefficient arrays,
+    with dC/dL of the exact-exponential coefficients for the kappa and alpha gradients."""
+    cfg = dict(_cfg(N, bc, kind, dim=dim, dt=0.02 if dim == 3 else 0.05), scheme="cox_matthews")
+    nsteps, K = (4, 3) if dim == 3 else (6, 4)
+    u0 = _fields(cfg, 5, kind)
+    target = _fields(cfg, 6, kind)
+    du0, da, dk, dp = _grads(cfg, u0, target, nsteps, K)
+    s = O.ETDRK4P13(oracle_problem(cfg), scheme="cox_matthews")
+    uT = s.run(list(u0), 0.0, nsteps)
+    ref = O.adjoint_run(s, list(u0), 0.0, nsteps, [a - b for a, b in zip(uT, target)],
+                        dparams=reaction_fns(cfg)[2])
+    ref_u0 = np.stack(ref["u0"])
+    assert float(np.max(np.abs(du0 - ref_u0)) / np.max(np.abs(ref_u0))) < 1e-9
+    for sp in range(2):
+        assert _rel(da[sp], ref["alpha"][sp]) < 1e-8
+        assert _rel(dk[sp], ref["kappa"][sp]) < 1e-8 or abs(dk[sp] - ref["kappa"][sp]) < 1e-12
+    h = 1e-6
+    a0, a1 = cfg["alpha"]
+    fd = (_loss(dict(cfg, alpha=(a0, a1 + h)), u0, target, nsteps)
+          - _loss(dict(cfg, alpha=(a0, a1 - h)), u0, target, nsteps)) / (2 * h)
+    assert _rel(da[1], fd) < 1e-6
+    k0, k1 = cfg["kappa"]
+    fd = (_loss(dict(cfg, kappa=(k0 + h, k1)), u0, target, nsteps)
+          - _loss(dict(cfg, kappa=(k0 - h, k1)), u0, target, nsteps)) / (2 * h)
+    assert _rel(dk[0], fd) < 1e-6
 
 
 def test_checkpoint_interval_does_not_change_gradients():

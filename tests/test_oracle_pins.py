@@ -631,6 +631,61 @@ def test_cox_matthews_and_p13_agree_to_fifth_order_in_l():
     assert d[1] / d[0] == pytest.approx(32.0, rel=0.05)
 
 
+def test_cox_matthews_derivatives_zero_limits_and_central_differences():
+    """dC/dL of the Cox-Matthews arrays: at L = 0 the values follow from the series by hand
+    (d e^{-L} = -1, d e^{-L/2} = -1/2, dphi = -tau/8, dphi1 = dphi2 = -tau/6, dphi3 = 0), and
+    elsewhere they equal central differences of cox_matthews_coefficients."""
+    tau = 0.1
+    d0 = O.cox_matthews_derivatives(np.array([0.0]), tau)
+    for k, v in (("R13", -1.0), ("Q13", -0.5), ("phi", -tau / 8), ("phi1", -tau / 6), ("phi2", -tau / 6)):
+        assert d0[k][0] == pytest.approx(v, rel=1e-13), k
+    assert abs(d0["phi3"][0]) < 1e-15
+    L = np.array([0.3, 0.99, 1.0, 1.5, 2.0, 2.5, 3.7, 30.0])
+    h = 1e-6
+    d = O.cox_matthews_derivatives(L, tau)
+    cp, cm = O.cox_matthews_coefficients(L + h, tau), O.cox_matthews_coefficients(L - h, tau)
+    for k in d:
+        fd = (cp[k] - cm[k]) / (2 * h)
+        np.testing.assert_allclose(d[k], fd, rtol=1e-7, atol=1e-12 * tau, err_msg=k)
+
+
+def test_oracle_cox_matthews_adjoint_matches_central_differences():
+    """The oracle's reverse sweep with the Cox-Matthews coefficients: dl/dalpha, dl/dkappa and
+    dl/du0 of l = 1/2 ||u_M - target||^2 through 3 steps against central differences."""
+    N = 6
+    g = O.Grid((N, N), (0.0, 0.0), (10.0, 10.0))
+    rng = np.random.default_rng(8)
+    f, J, dmu = O.fitzhugh_nagumo()
+
+    def build(alpha, kappa_u):
+        prob = O.Problem(g, O.NEUMANN, [alpha, alpha], [kappa_u, 0.3], 0.1, f, dreaction=J)
+        return O.ETDRK4P13(prob, scheme="cox_matthews")
+
+    shp = g.shape(O.NEUMANN)
+    u0 = [rng.uniform(0, 1, shp), rng.uniform(0, 0.2, shp)]
+    tgt = [rng.uniform(0, 1, shp), rng.uniform(0, 0.2, shp)]
+    M = 3
+
+    def loss(alpha, kappa_u, u0_):
+        uM = build(alpha, kappa_u).run(u0_, 0.0, M)
+        return 0.5 * sum(float(np.sum((a - b) ** 2)) for a, b in zip(uM, tgt))
+
+    s = build(1.6, 1.0)
+    uM = s.run(u0, 0.0, M)
+    gr = O.adjoint_run(s, u0, 0.0, M, [a - b for a, b in zip(uM, tgt)], dparams=dmu)
+    hh = 1e-6
+    fd = (loss(1.6 + hh, 1.0, u0) - loss(1.6 - hh, 1.0, u0)) / (2 * hh)
+    assert sum(gr["alpha"]) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    fd = (loss(1.6, 1.0 + hh, u0) - loss(1.6, 1.0 - hh, u0)) / (2 * hh)
+    assert gr["kappa"][0] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    up = [x.copy() for x in u0]
+    um = [x.copy() for x in u0]
+    up[0][2, 3] += hh
+    um[0][2, 3] -= hh
+    fd = (loss(1.6, 1.0, up) - loss(1.6, 1.0, um)) / (2 * hh)
+    assert gr["u0"][0][2, 3] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
 # --------------------------------------------------------------------------
 # Section 5: the error norms every parity test decides by
 # --------------------------------------------------------------------------
