@@ -15,6 +15,7 @@ namespace sfrd {
 
 struct BatchItem {
     int inst, bx, by, cost;
+    int bz;   // species of an element-pair tile (0 otherwise)
 };
 
 template <typename T> struct BatchX {
@@ -76,7 +77,9 @@ __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>()))
                [&](const XArgs<T>& a, const BatchItem& it) { x2_body<T, N, MODE>(a, it.bx, smem_raw); });
 }
 
-template <typename T, int N, int MODE>
+// PAIR: the stage passes of FP32 two-species instances on element pairs (species = item.bz), as the
+// single-instance slow-axis passes run them.
+template <typename T, int N, int MODE, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>()))
     batch_col2_kernel(const BatchC<T>* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
                       int* counter) {
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>()))
     __shared__ __align__(16) ColArgs<T> s_args;
     __shared__ int s_w;
     batch_loop<false>(insts, items, nitems, counter, 0.0, &s_args, &s_w, [&](const ColArgs<T>& a, const BatchItem& it) {
-        col2_body<T, N, MODE>(a, it.bx, it.by, smem_raw);
+        col2_body<T, N, MODE, -1, false, PAIR>(a, it.bx, it.by, smem_raw, it.bz);
     });
 }
 
@@ -99,10 +102,21 @@ inline int batch_grid(const void* kernel, size_t smem, int blocks_per_sm, int sm
     return (int)(g < nitems ? g : nitems);
 }
 
-// Kernel of the length-N batched pass of kind `axis` and `mode`.
+// Kernel of the length-N batched pass of kind `axis` and `mode` (`pair`: the element-pair stage passes).
 template <typename T, int N>
-const void* batch_kernel2(int axis, int mode) {
+const void* batch_kernel2(int axis, int mode, bool pair = false) {
     if (axis == BATCH_X) return reinterpret_cast<const void*>(batch_x2_kernel<T, N, MODE_REACT>);
+    if constexpr (sizeof(T) == 4) {
+        if (pair) {
+            switch (mode) {
+                case MODE_TA: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TA, true>);
+                case MODE_TB: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TB, true>);
+                case MODE_TC: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TC, true>);
+                case MODE_TD: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TD, true>);
+                default: break;
+            }
+        }
+    }
     switch (mode) {
         case MODE_PLAIN: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_PLAIN>);
         case MODE_TA: return reinterpret_cast<const void*>(batch_col2_kernel<T, N, MODE_TA>);
@@ -115,7 +129,7 @@ const void* batch_kernel2(int axis, int mode) {
 // Grids of the length-N batched launches (taken when the batch is bound, outside any capture):
 // grid[0] the x pass, grid[1 + m] the column pass of mode m in (PLAIN, TA, TB, TC, TD).
 template <typename T, int N>
-cudaError_t batch_grids2(int axis, int blocks_per_sm, int sms, int nitems, int* grid) {
+cudaError_t batch_grids2(int axis, int blocks_per_sm, int sms, int nitems, int* grid, bool pair) {
     const size_t smem = TileOf<T, N>::E::smem_bytes();
     cudaError_t e = cudaSuccess;
     if (axis == BATCH_X) {
@@ -124,14 +138,14 @@ cudaError_t batch_grids2(int axis, int blocks_per_sm, int sms, int nitems, int* 
     }
     const int modes[5] = {MODE_PLAIN, MODE_TA, MODE_TB, MODE_TC, MODE_TD};
     for (int m = 0; m < 5 && e == cudaSuccess; ++m)
-        grid[1 + m] = batch_grid(batch_kernel2<T, N>(BATCH_COL, modes[m]), smem, blocks_per_sm, sms, nitems, &e);
+        grid[1 + m] = batch_grid(batch_kernel2<T, N>(BATCH_COL, modes[m], pair), smem, blocks_per_sm, sms, nitems, &e);
     return e;
 }
 
 // One launch of the length-N kernel of pass kind `axis` and `mode` on stream s, `grid` blocks.
 template <typename T, int N>
 cudaError_t batch_launch2(int axis, int mode, const void* args, const BatchItem* items, int nitems, double frac,
-                          int* counter, int grid, cudaStream_t s) {
+                          int* counter, int grid, cudaStream_t s, bool pair) {
     const size_t smem = TileOf<T, N>::E::smem_bytes();
     if (axis == BATCH_X) {
         batch_x2_kernel<T, N, MODE_REACT><<<grid, kThreads, smem, s>>>(static_cast<const BatchX<T>*>(args), items,
@@ -139,7 +153,7 @@ cudaError_t batch_launch2(int axis, int mode, const void* args, const BatchItem*
         return cudaGetLastError();
     }
     auto k = reinterpret_cast<void (*)(const BatchC<T>*, const BatchItem*, int, int*)>(
-        const_cast<void*>(batch_kernel2<T, N>(BATCH_COL, mode)));
+        const_cast<void*>(batch_kernel2<T, N>(BATCH_COL, mode, pair)));
     k<<<grid, kThreads, smem, s>>>(static_cast<const BatchC<T>*>(args), items, nitems, counter);
     return cudaGetLastError();
 }
@@ -155,13 +169,20 @@ cudaError_t batch_prepare2() {
         batch_col2_kernel<T, N, MODE_TC>, batch_col2_kernel<T, N, MODE_TD>};
     for (auto k : ks)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+    if constexpr (sizeof(T) == 4) {
+        void (*kp[])(const BatchC<T>*, const BatchItem*, int, int*) = {
+            batch_col2_kernel<T, N, MODE_TA, true>, batch_col2_kernel<T, N, MODE_TB, true>,
+            batch_col2_kernel<T, N, MODE_TC, true>, batch_col2_kernel<T, N, MODE_TD, true>};
+        for (auto k : kp)
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+    }
     return e;
 }
 
 #define SFRD_BATCH_INSTANTIATE(T, N)                                                                     \
-    template cudaError_t batch_grids2<T, N>(int, int, int, int, int*);                                    \
+    template cudaError_t batch_grids2<T, N>(int, int, int, int, int*, bool);                              \
     template cudaError_t batch_launch2<T, N>(int, int, const void*, const BatchItem*, int, double, int*, int, \
-                                             cudaStream_t);                                               \
+                                             cudaStream_t, bool);                                         \
     template cudaError_t batch_prepare2<T, N>();
 
 }  // namespace v2

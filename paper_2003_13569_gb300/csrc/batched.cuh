@@ -26,9 +26,9 @@ constexpr int kBatchMaxN = 512;
 
 namespace v2 {
 #define SFRD_BATCH_EXTERN(T, N)                                                                                \
-    extern template cudaError_t batch_grids2<T, N>(int, int, int, int, int*);                                   \
+    extern template cudaError_t batch_grids2<T, N>(int, int, int, int, int*, bool);                             \
     extern template cudaError_t batch_launch2<T, N>(int, int, const void*, const BatchItem*, int, double, int*, \
-                                                    int, cudaStream_t);                                         \
+                                                    int, cudaStream_t, bool);                                   \
     extern template cudaError_t batch_prepare2<T, N>();
 #define SFRD_BATCH_EXTERN_ALL(T)                                                                     \
     SFRD_BATCH_EXTERN(T, 64) SFRD_BATCH_EXTERN(T, 96) SFRD_BATCH_EXTERN(T, 128) SFRD_BATCH_EXTERN(T, 200) \
@@ -85,6 +85,7 @@ struct BatchGroup {
     int nitems = 0;
     size_t smem = 0;   // shared-memory engine: the largest tile of its instances
     int grid[6] = {0, 0, 0, 0, 0, 0};   // x pass, then column modes PLAIN, TA, TB, TC, TD (set at bind)
+    bool pair = false;   // register-engine stage passes on element pairs (FP32 two-species instances)
 };
 
 // Device tables of one batched pass kind.
@@ -155,18 +156,22 @@ static void batch_tables(BatchPlan& b, std::vector<char>& host) {
         xa[i].a = x_args<T>(p, W, W, p.pitch, 0.0, g);
         xa[i].engine = p.v2[0] ? 1 : 0;
         xa[i].N = (int)p.Nint[0];
-        for (unsigned bx = 0; bx < g.x; ++bx) xi[i].push_back(BatchItem{i, (int)bx, 0, (int)p.Nint[0]});
-        sa[i].a = col_args<T>(p, slow, W, W, 1.0, g);
+        for (unsigned bx = 0; bx < g.x; ++bx) xi[i].push_back(BatchItem{i, (int)bx, 0, (int)p.Nint[0], 0});
+        // the batched step runs only the stage modes on the slow axis: element pairs where the
+        // single-instance step uses them (species on grid z)
+        sa[i].a = col_args<T>(p, slow, W, W, 1.0, g, true);
         sa[i].engine = p.v2[slow] ? 1 : 0;
         sa[i].N = (int)p.Nint[slow];
-        for (unsigned by = 0; by < g.y; ++by)
-            for (unsigned bx = 0; bx < g.x; ++bx) si[i].push_back(BatchItem{i, (int)bx, (int)by, (int)p.Nint[slow]});
+        for (unsigned bz = 0; bz < g.z; ++bz)
+            for (unsigned by = 0; by < g.y; ++by)
+                for (unsigned bx = 0; bx < g.x; ++bx)
+                    si[i].push_back(BatchItem{i, (int)bx, (int)by, (int)p.Nint[slow], (int)bz});
         if (b.dim == 3) {
             ma[i].a = col_args<T>(p, 1, W, W, 1.0, g);
             ma[i].engine = p.v2[1] ? 1 : 0;
             ma[i].N = (int)p.Nint[1];
             for (unsigned by = 0; by < g.y; ++by)
-                for (unsigned bx = 0; bx < g.x; ++bx) mi[i].push_back(BatchItem{i, (int)bx, (int)by, (int)p.Nint[1]});
+                for (unsigned bx = 0; bx < g.x; ++bx) mi[i].push_back(BatchItem{i, (int)bx, (int)by, (int)p.Nint[1], 0});
         }
     }
     size_t o = 0;
@@ -177,19 +182,26 @@ static void batch_tables(BatchPlan& b, std::vector<char>& host) {
         std::memcpy(host.data() + at, src, bytes);
         return at;
     };
-    auto groups = [&](BatchPass& ps, int d, const std::vector<std::vector<BatchItem>>& items) {
+    auto groups = [&](BatchPass& ps, int d, const std::vector<std::vector<BatchItem>>& items,
+                      const std::vector<BatchC<T>>* cargs) {
         ps.groups.clear();
         for (const auto& key : group_keys(b.inst, d)) {
             BatchGroup gr;
             gr.engine = key.first;
             gr.N = key.second;
             std::vector<BatchItem> its;
+            int npair = 0, nmember = 0;
             for (int i = 0; i < n; ++i) {
                 const Plan& p = b.inst[i];
                 if ((p.v2[d] ? 1 : 0) != key.first || (key.first && (int)p.Nint[d] != key.second)) continue;
                 its.insert(its.end(), items[i].begin(), items[i].end());
                 gr.smem = std::max(gr.smem, inst_smem<T>(p, d));
+                ++nmember;
+                if (cargs && (*cargs)[i].a.in_sp > 0) ++npair;
             }
+            // one kernel per group: the pair layout depends only on the batch's dtype and species count
+            // and on the register engine (col_args), so a group's instances all have it or none does
+            gr.pair = key.first == 1 && npair > 0 && npair == nmember;
             // longest lines first (the shared-memory group mixes lengths)
             std::stable_sort(its.begin(), its.end(),
                              [](const BatchItem& x, const BatchItem& y) { return x.cost > y.cost; });
@@ -199,12 +211,12 @@ static void batch_tables(BatchPlan& b, std::vector<char>& host) {
         }
     };
     b.px.off_args = put(xa.data(), xa.size() * sizeof(BatchX<T>));
-    groups(b.px, 0, xi);
+    groups(b.px, 0, xi, nullptr);
     b.pslow.off_args = put(sa.data(), sa.size() * sizeof(BatchC<T>));
-    groups(b.pslow, slow, si);
+    groups(b.pslow, slow, si, &sa);
     if (b.dim == 3) {
         b.pmid.off_args = put(ma.data(), ma.size() * sizeof(BatchC<T>));
-        groups(b.pmid, 1, mi);
+        groups(b.pmid, 1, mi, nullptr);
     } else {
         b.pmid.off_args = 0;
         b.pmid.groups.clear();
@@ -244,7 +256,7 @@ static cudaError_t batch_set_grids(BatchPlan& b) {
             if (gr.engine == 1) {
                 switch (gr.N) {
 #define SFRD_BATCH_CASE(N) \
-    case N: SFRD_TRY((v2::batch_grids2<T, N>(axis, b.blocks_per_sm, b.sms, gr.nitems, gr.grid))); break;
+    case N: SFRD_TRY((v2::batch_grids2<T, N>(axis, b.blocks_per_sm, b.sms, gr.nitems, gr.grid, gr.pair))); break;
                     SFRD_BATCH_CASE(64) SFRD_BATCH_CASE(96) SFRD_BATCH_CASE(128) SFRD_BATCH_CASE(200)
                     SFRD_BATCH_CASE(256) SFRD_BATCH_CASE(384) SFRD_BATCH_CASE(512)
 #undef SFRD_BATCH_CASE
@@ -278,7 +290,7 @@ static cudaError_t batch_launch_group(const BatchPlan& b, const BatchPass& ps, c
     if (gr.engine == 1) {
         switch (gr.N) {
 #define SFRD_BATCH_CASE(N) \
-    case N: return v2::batch_launch2<T, N>(axis, mode, args, items, gr.nitems, frac, counter, grid, s);
+    case N: return v2::batch_launch2<T, N>(axis, mode, args, items, gr.nitems, frac, counter, grid, s, gr.pair);
             SFRD_BATCH_CASE(64) SFRD_BATCH_CASE(96) SFRD_BATCH_CASE(128) SFRD_BATCH_CASE(200)
             SFRD_BATCH_CASE(256) SFRD_BATCH_CASE(384) SFRD_BATCH_CASE(512)
 #undef SFRD_BATCH_CASE

@@ -231,12 +231,49 @@ struct Eng {
         return cfma(dif, -s, cscale(cadd(xj, xm), (T)0.5));
     }
 
+    // Pre-processing of a mirror pair: z_j and z_{N-j} from the line's values xj, xm at transform
+    // indices j and N - j (x_0 = x_N = 0 for Dirichlet; xm unused for periodic), with s = sin(j pi/N) and
+    // co = cos(j pi/N); the Neumann anchor gains this pair's share (x_j - x_{N-j}) cos(j pi/N), or
+    // (x_0 - x_N)/2 for j = 0.  One thread then writes both, so every value is read once.
+    static __device__ __forceinline__ void pre_pair(int bc_, int j, C xj, C xm, T s, T co, C& zj, C& zm, C& anchor) {
+        const int bc = bcv(bc_);
+        if (bc == SFRD_BC_PERIODIC) {
+            zj = xj;
+            zm = xm;
+            return;
+        }
+        const C sum = cadd(xj, xm), dif = csub(xj, xm);
+        if (bc == SFRD_BC_DIRICHLET) {
+            const C o = cscale(dif, (T)0.5);
+            zj = cfma(sum, s, o);
+            zm = cfma(sum, s, cneg(o));
+            return;
+        }
+        const C e = cscale(sum, (T)0.5);
+        zj = cfma(dif, -s, e);
+        zm = cfma(dif, s, e);
+        anchor = j == 0 ? cfma(dif, (T)0.5, anchor) : cfma(dif, co, anchor);
+    }
+
+    // forward() for a buffer that already holds the pre-processed line z (natural order, written with
+    // pre_pair) and red2 the Neumann anchor parts.  Entry: z complete (after a barrier).
+    static __device__ __forceinline__ void forward_z(C* buf, int bc_, const C* tws, int twstride_, int c, int g) {
+        forward_impl<true>(buf, nullptr, bc_, tws, twstride_, c, g);
+    }
+
     // V (natural, unknown index) -> pre-processing -> DFT_N -> Z (natural order).
     // Entry: V complete (after a barrier).  Exit: Z complete (after a barrier).
     // red2[g][c] receives this thread's part of the Neumann anchor.
     // tws: the axis table in shared memory, omega_{N*twstride}^m (twstride = 1 periodic, 2 otherwise).
     static __device__ __forceinline__ void forward(C* buf, C* red2, int bc_, const C* tws, int twstride_, int c,
                                                    int g) {
+        forward_impl<false>(buf, red2, bc_, tws, twstride_, c, g);
+    }
+
+    // ZIN: the buffer holds z already (forward_z); else the values V, pre-processed on the way in.
+    template <bool ZIN>
+    static __device__ __forceinline__ void forward_impl(C* buf, C* red2, int bc_, const C* tws, int twstride_, int c,
+                                                        int g) {
         const int bc = bcv(bc_);
         const int twstride = BCT < 0 ? twstride_ : (BCT == SFRD_BC_PERIODIC ? 1 : 2);
         C a[NO1][R1];
@@ -245,8 +282,10 @@ struct Eng {
         for (int o = 0; o < NO1; ++o) {
             const int n2 = g + o * G;
             if (R2 % G == 0 || n2 < R2) {
+                if constexpr (ZIN) {
 #pragma unroll
-                {
+                    for (int n1 = 0; n1 < R1; ++n1) a[o][n1] = buf[(R2 * n1 + n2) * LD + c];
+                } else {
                     // w_j for j = R2 n1 + n2 by rotating w_{n2} (one table read) through the
                     // compile-time angle R2 n1 pi / N
                     const C wb = bc == SFRD_BC_PERIODIC ? czero<C>() : tws[n2];
@@ -282,7 +321,7 @@ struct Eng {
                 }
             }
         }
-        red2[g * CC + c] = anchor;
+        if constexpr (!ZIN) red2[g * CC + c] = anchor;
         __syncthreads();   // all reads of V done: the buffer becomes Z
 #pragma unroll
         for (int o = 0; o < NO1; ++o) {

@@ -77,6 +77,7 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
     const size_t org_in = (size_t)by * (size_t)a.in_sOther + (size_t)xA + (size_t)bz * (size_t)a.in_sp;
     const size_t org_out = (size_t)by * (size_t)a.out_sOther + (size_t)xA + (size_t)bz * (size_t)a.out_sp;
     const unsigned s_in = (unsigned)a.in_sAxis, s_out = (unsigned)a.out_sAxis;
+    bool zin = false;   // the buffer holds the pre-processed line (forward_z)
 
     if constexpr (PAIR) {
         // element pairs (internal arrays, even pitch: x < pitch implies x + 1 < pitch; 8-byte aligned);
@@ -118,6 +119,56 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
             const int i = (w * RPI + sub) + r * NW * RPI;
             if (i < n) dst[2 * i * LD] = v[r];
         }
+    } else if (MODE == MODE_PLAIN && a.cstride == 2) {
+        // lines A and B are the adjacent columns x, x + 1: one 2-element load per row where aligned.
+        // Each thread loads the mirror pairs (j, N - j), j = g, g + G, ..., N/2, and writes their
+        // pre-processed values z_j, z_{N-j}, so the transform reads every value once.
+        constexpr int NP = (N / 2 + 1 + G - 1) / G;
+        const bool okA = xA < a.in_xlim, okB = xB < a.in_xlim;
+        const T* pA = a.in + org_in;
+        const bool vec = okB && ((a.in_sAxis | a.in_sOther) & 1) == 0 &&
+                         (reinterpret_cast<uintptr_t>(a.in) % sizeof(C)) == 0;
+        const int bcx = E::bcv(bc);
+        // value at transform index q (0 <= q <= N): unknown q - 1 (Dirichlet, zero at q = 0, N), else q
+        auto val = [&](int q) {
+            const int i = bcx == SFRD_BC_DIRICHLET ? q - 1 : q;
+            C z = czero<C>();
+            if (i >= 0 && i < n) {
+                const unsigned o = (unsigned)i * s_in;
+                if (vec) {
+                    z = *reinterpret_cast<const C*>(pA + o);
+                } else {
+                    z.x = okA ? pA[o] : (T)0;
+                    z.y = okB ? pA[o + 1] : (T)0;
+                }
+            }
+            return z;
+        };
+        C xj[NP], xm[NP];
+#pragma unroll
+        for (int t = 0; t < NP; ++t) {
+            const int j = g + t * G;
+            xj[t] = czero<C>();
+            xm[t] = czero<C>();
+            if (j <= N / 2) {
+                xj[t] = val(j);
+                xm[t] = val(N - j);
+            }
+        }
+        C anchor = czero<C>();
+#pragma unroll
+        for (int t = 0; t < NP; ++t) {
+            const int j = g + t * G;
+            if (j <= N / 2) {
+                const C w = bcx == SFRD_BC_PERIODIC ? czero<C>() : __ldg(tw + j);   // (cos, -sin)(j pi / N)
+                C zj, zm;
+                E::pre_pair(bc, j, xj[t], xm[t], -w.y, w.x, zj, zm, anchor);
+                buf[j * LD + c] = zj;
+                if (j > 0 && j < N / 2) buf[(N - j) * LD + c] = zm;
+            }
+        }
+        red2[g * CC + c] = anchor;
+        zin = true;
     } else if (MODE == MODE_PLAIN && a.cstride == 2) {
         // lines A and B are the adjacent columns x, x + 1: one 2-element load per row where aligned
         constexpr int NL = (E::ROWS + G - 1) / G;
@@ -163,7 +214,8 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
         }
     }
     __syncthreads();
-    E::forward(buf, red2, bc, tws, twstride, c, g);
+    if (zin) E::forward_z(buf, bc, tws, twstride, c, g);
+    else E::forward(buf, red2, bc, tws, twstride, c, g);
 
     if (MODE == MODE_PLAIN && a.cstride == 2) {
         // adjacent columns: one 2-element store per output where aligned
@@ -703,7 +755,7 @@ cudaError_t prepare2_bc() {
 
 template <typename T, int N>
 cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
-    if (BcSpecialised<T, N>::value) {
+    if constexpr (BcSpecialised<T, N>::value) {
         switch (a.ax.bc) {
             case SFRD_BC_PERIODIC: return col2_launch_bc<T, N, SFRD_BC_PERIODIC>(a, mode, grid, s);
             case SFRD_BC_DIRICHLET: return col2_launch_bc<T, N, SFRD_BC_DIRICHLET>(a, mode, grid, s);
@@ -715,7 +767,7 @@ cudaError_t col2_launch(const ColArgs<T>& a, int mode, dim3 grid, cudaStream_t s
 
 template <typename T, int N>
 cudaError_t x2_launch(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
-    if (BcSpecialised<T, N>::value) {
+    if constexpr (BcSpecialised<T, N>::value) {
         switch (a.ax.bc) {
             case SFRD_BC_PERIODIC: return x2_launch_bc<T, N, SFRD_BC_PERIODIC>(a, mode, grid, s);
             case SFRD_BC_DIRICHLET: return x2_launch_bc<T, N, SFRD_BC_DIRICHLET>(a, mode, grid, s);
@@ -727,7 +779,7 @@ cudaError_t x2_launch(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
 
 template <typename T, int N>
 cudaError_t prepare2() {
-    if (BcSpecialised<T, N>::value) {
+    if constexpr (BcSpecialised<T, N>::value) {
         cudaError_t e = prepare2_bc<T, N, SFRD_BC_PERIODIC>();
         if (e == cudaSuccess) e = prepare2_bc<T, N, SFRD_BC_DIRICHLET>();
         if (e == cudaSuccess) e = prepare2_bc<T, N, SFRD_BC_NEUMANN>();
