@@ -156,17 +156,23 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
             }
         }
         C anchor = czero<C>();
-#pragma unroll
-        for (int t = 0; t < NP; ++t) {
+        // (cos, -sin)(j pi / N) for j = g + t G: the table value at g rotated through the compile-time
+        // angle t G pi / N (one table read per thread)
+        const C wg = bcx == SFRD_BC_PERIODIC ? czero<C>() : __ldg(tw + g);
+        static_for<0, NP>([&](auto TT) {
+            constexpr int t = decltype(TT)::value;
             const int j = g + t * G;
             if (j <= N / 2) {
-                const C w = bcx == SFRD_BC_PERIODIC ? czero<C>() : __ldg(tw + j);   // (cos, -sin)(j pi / N)
+                constexpr T cr = (T)ce_cs2pi(t * G, 2 * N).c, ci = (T)(-ce_cs2pi(t * G, 2 * N).s);
+                C w;
+                w.x = wg.x * cr - wg.y * ci;
+                w.y = wg.x * ci + wg.y * cr;
                 C zj, zm;
                 E::pre_pair(bc, j, xj[t], xm[t], -w.y, w.x, zj, zm, anchor);
                 buf[j * LD + c] = zj;
                 if (j > 0 && j < N / 2) buf[(N - j) * LD + c] = zm;
             }
-        }
+        });
         red2[g * CC + c] = anchor;
         zin = true;
     } else if (MODE == MODE_PLAIN && a.cstride == 2) {

@@ -27,3 +27,20 @@ def test_zero_steps_return_the_input(dim, N, bc, kind, dtype, tol):
     got = _np(sf.Solver(cfg, dtype=dtype).run(u0, nsteps=0)).astype(np.float64)
     assert got.shape == u0.shape
     assert rel_max(got, u0) < tol
+
+
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet", "neumann"])
+@pytest.mark.parametrize("Ns", [(2,), (3,), (5,), (2, 2), (2, 3), (4, 5), (2, 3, 4), (4, 2, 3), (5, 5, 2)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_smallest_grids_match_the_oracle(bc, Ns, dtype, tol):
+    """Degenerate sizes: 2-5 intervals per axis (one to six unknowns), 1D to 3D, every boundary condition,
+    a two-species reaction, several steps, against the oracle (the shared-memory engine's smallest
+    transforms, single-row and single-column tiles)."""
+    import oracle as O
+    from oracle.bridge import solver as oracle_solver
+    cfg = _cfg(len(Ns), Ns, bc, kind="fhn", dt=0.05)
+    u0 = _rand_fields(cfg, seed=sum(Ns), lo=0.0, hi=1.0)
+    got = _np(sf.Solver(cfg, dtype=dtype).run(np.stack(u0), nsteps=5)).astype(np.float64)
+    ref = oracle_solver(cfg).run(u0, 0.0, 5)
+    err = O.rel_max(list(got), ref) if dtype == "f64" else O.rel_l2(list(got), ref)
+    assert err < tol, err
