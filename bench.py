@@ -197,40 +197,55 @@ def cpu_baseline(cfg, seconds):
     el = time.perf_counter() - t0
     dof = int(np.prod(W.field_shape(cfg))) * 2
     return {"value": dof * n / el, "unit": "DOF-steps/s", "cores": os.cpu_count(), "cpu_model": cpu_model(),
-            "kind": "oracle",
+            "kind": "oracle", "role": "the stated host baseline: whole steps of the full workload",
             "sample": "%d ETDRK4-P13 step(s) of the full %s workload, FP64 dense-matrix oracle, %.1f s"
                       % (n, "x".join(str(x) for x in W.field_shape(cfg)), el)}
 
 
 def reference_arm(args):
-    """--impl reference: the CPU oracle on a bounded sample of the workload per step."""
+    """--impl reference: the CPU oracle on the workload per step, timed on the host cores.
+
+    The full 255^3 grid is used when the whole --warmup/--steps run fits in about four minutes at the
+    measured time of one oracle step (one untimed step first); otherwise the largest of the reduced grids
+    N = 128, 64 that fits, named in config.sample_grid (same_config false)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # per step: one oracle ETDRK4 step on a reduced grid of the same workload so that
-    # the whole --steps/--warmup run stays within a few minutes
-    Nsample = int(os.environ.get("SFRD_REF_N", "64"))
-    cfg = W.scaled(WORKLOAD, Nsample)
     from oracle.bridge import solver as oracle_solver
-    s = oracle_solver(cfg)
-    u = W.initial_fields(cfg)
+    budget = float(os.environ.get("SFRD_REF_SECONDS", "240"))
+    nrun = args.warmup + args.steps
+    cfg = None
+    sizes = (W.config(WORKLOAD)["N"][0], 128, 64)
+    if os.environ.get("SFRD_REF_N"):             # a fixed sample size (the CPU tests use a tiny one)
+        sizes = (int(os.environ["SFRD_REF_N"]),)
+    for Nsample in sizes:
+        c = W.scaled(WORKLOAD, Nsample)
+        s = oracle_solver(c)
+        u = W.initial_fields(c)
+        t0 = time.perf_counter()
+        u = s.step(u, 0.0)                       # untimed: the cost of one step at this size
+        if (time.perf_counter() - t0) * nrun <= budget or Nsample == sizes[-1]:
+            cfg = c
+            break
     for k in range(args.warmup):
-        u = s.step(u, k * cfg["dt"])
+        u = s.step(u, (k + 1) * cfg["dt"])
     t0 = time.perf_counter()
     for k in range(args.steps):
-        u = s.step(u, k * cfg["dt"])
+        u = s.step(u, (args.warmup + 1 + k) * cfg["dt"])
     el = time.perf_counter() - t0
     dof = int(np.prod(W.field_shape(cfg))) * 2
     v = dof * args.steps / el
+    full = cfg["N"] == W.config(WORKLOAD)["N"]
+    n1 = cfg["N"][0] - 1
     line = {"metric": METRIC, "value": v, "unit": "DOF-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": workload_desc(W.config(WORKLOAD)),
-                       "sample_grid": list(cfg["N"]), "parallelism": "replicas"},
+                       "sample_grid": list(cfg["N"]), "same_config": full, "parallelism": "replicas"},
             "cpu_baseline": {"value": v, "unit": "DOF-steps/s", "cores": os.cpu_count(), "cpu_model": cpu_model(),
                              "kind": "oracle",
                              "sample": "one FP64 oracle step per bench step on the same workload at N=%d "
-                                       "(%d^3 interior)" % (Nsample, Nsample - 1)},
+                                       "(%d^3 interior)" % (cfg["N"][0], n1)},
             "e2e": {"value": v, "unit": "DOF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
