@@ -363,7 +363,8 @@ int sfrd_batch_store(sfrd_batch_t batch, void* const* u);
  * per batched step (a NULL output pointer is skipped). */
 int sfrd_batch_info(sfrd_batch_t batch, int64_t* count, int64_t* dof, int64_t* launches_per_step);
 /* Autotuner of the batched schedule: times `steps` batched steps for each
- * number of resident blocks per SM (1..4) of the persistent launches and each
+ * number of resident blocks per SM (1..4) of the persistent column-pass launches
+ * (the x-pass launches run at their kernel's full occupancy) and each
  * radix-stage order of the instances on the shared-memory engine, and keeps the
  * fastest.  The batch must be bound; it is bound again, so the instances must
  * be loaded afterwards.  chosen (may be NULL) receives {blocks per SM, order

@@ -266,8 +266,7 @@ static cudaError_t batch_set_grids(BatchPlan& b) {
             }
             cudaError_t e = cudaSuccess;
             if (axis == BATCH_X) {
-                gr.grid[0] = v2::batch_grid(reinterpret_cast<const void*>(kx), gr.smem, b.blocks_per_sm, b.sms,
-                                            gr.nitems, &e);
+                gr.grid[0] = v2::batch_grid(reinterpret_cast<const void*>(kx), gr.smem, 0, b.sms, gr.nitems, &e);
             } else {
                 for (int m = 0; m < 5 && e == cudaSuccess; ++m)
                     gr.grid[1 + m] = v2::batch_grid(reinterpret_cast<const void*>(kc[m]), gr.smem, b.blocks_per_sm,
