@@ -467,7 +467,11 @@ __device__ __forceinline__ void col2_body(const ColArgs<T>& a, int bx, int by, u
 template <typename T, int N, int MODE, int BCT = -1, bool RAT = false, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) col2_kernel(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    col2_body<T, N, MODE, BCT, RAT, PAIR>(a, blockIdx.x, blockIdx.y, smem_raw, blockIdx.z);
+    // The middle-axis pass takes its planes in reverse order: it then starts on those its producer (the
+    // slow-axis or the x pass) wrote last, still in L2, and leaves to the next pass the planes that pass
+    // reads first (255^3 step -2.7 %: y -5 %, x -2 %, slow-axis stages -2 %).
+    const int by = MODE == MODE_PLAIN ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+    col2_body<T, N, MODE, BCT, RAT, PAIR>(a, blockIdx.x, by, smem_raw, blockIdx.z);
 }
 
 template <typename T, int N, int MODE, int BCT = -1>
