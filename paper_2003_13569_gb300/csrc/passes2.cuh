@@ -474,7 +474,12 @@ __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) col2_ker
     col2_body<T, N, MODE, BCT, RAT, PAIR>(a, blockIdx.x, by, smem_raw, blockIdx.z);
 }
 
-template <typename T, int N, int MODE, int BCT = -1>
+// Lengths whose contiguous-axis pass is also compiled once per two-species reaction kind (KIND >= 0: the
+// reaction of that kind only, no stage save), so that the kernel holds one reaction unpacking instead of
+// all of them: at length 1024 the unrolled unpackings of every kind exceed the instruction cache.
+template <typename T, int N> struct KindSpecialised { static constexpr bool value = sizeof(T) == 4 && N == 1024; };
+
+template <typename T, int N, int MODE, int BCT = -1, int KIND = -1>
 __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char* smem_raw) {
     constexpr int CC = TileOf<T, N>::CC;
     using E = typename TileOf<T, N, BCT>::E;
@@ -527,7 +532,14 @@ __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char
     if (MODE == MODE_REACT) {
         const int rA = r0 + c, rB = rA + shiftB;
         T* sv = a.save ? a.save + (long long)rA * a.out_pitch : nullptr;   // stage save (adjoint recomputation)
-        if (a.S == 2 && !sv) {
+        if constexpr (KIND >= 0) {
+            // the launch has checked: two species, no stage save, reaction kind KIND
+            E::post(buf, red, red2, bc, c, g, [&](int i, C v) {
+                C f;
+                react2k<T>(KIND, a.re, v.x, v.y, f.x, f.y);
+                buf[i * LD + c] = f;
+            });
+        } else if (a.S == 2 && !sv) {
             // two-species kinds: the pointwise reaction is applied to each physical value as the
             // transform unpacks it (one unpacking per kind, so that the kind is a compile-time constant)
             auto run = [&](auto kind) {
@@ -596,10 +608,10 @@ __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char
     }
 }
 
-template <typename T, int N, int MODE, int BCT = -1>
+template <typename T, int N, int MODE, int BCT = -1, int KIND = -1>
 __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) x2_kernel(const XArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    x2_body<T, N, MODE, BCT>(a, blockIdx.x, smem_raw);
+    x2_body<T, N, MODE, BCT, KIND>(a, blockIdx.x, smem_raw);
 }
 
 // ---- launch --------------------------------------------------------------------------
@@ -725,11 +737,27 @@ cudaError_t col2_rat_prepare_bc() {
     return cudaSuccess;
 }
 
+// The reaction pass of one two-species kind (the kinds of react2k; any other kind has no reaction there).
+template <typename T, int N, int BCT>
+void (*x2_kind_kernel(int kind))(const XArgs<T>) {
+    switch (kind) {
+        case SFRD_REACT_SCHNAKENBERG: return x2_kernel<T, N, MODE_REACT, BCT, SFRD_REACT_SCHNAKENBERG>;
+        case SFRD_REACT_GRAY_SCOTT: return x2_kernel<T, N, MODE_REACT, BCT, SFRD_REACT_GRAY_SCOTT>;
+        case SFRD_REACT_FHN: return x2_kernel<T, N, MODE_REACT, BCT, SFRD_REACT_FHN>;
+        case SFRD_REACT_GIERER_MEINHARDT: return x2_kernel<T, N, MODE_REACT, BCT, SFRD_REACT_GIERER_MEINHARDT>;
+        case SFRD_REACT_LINEAR: return x2_kernel<T, N, MODE_REACT, BCT, SFRD_REACT_LINEAR>;
+        default: return x2_kernel<T, N, MODE_REACT, BCT, SFRD_REACT_NONE>;
+    }
+}
+
 template <typename T, int N, int BCT>
 cudaError_t x2_launch_bc(const XArgs<T>& a, int mode, dim3 grid, cudaStream_t s) {
     const size_t smem = TileOf<T, N>::E::smem_bytes();
     void (*k)(const XArgs<T>) =
         mode == MODE_REACT ? x2_kernel<T, N, MODE_REACT, BCT> : x2_kernel<T, N, MODE_PLAIN, BCT>;
+    if constexpr (KindSpecialised<T, N>::value) {
+        if (mode == MODE_REACT && a.S == 2 && !a.save) k = x2_kind_kernel<T, N, BCT>(a.re.kind);
+    }
     k<<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -740,6 +768,14 @@ cudaError_t x2_prepare_bc() {
     for (auto k : xs) {
         const cudaError_t e = set_smem_attrs(k, kMaxDynSmem2);
         if (e != cudaSuccess) return e;
+    }
+    if constexpr (KindSpecialised<T, N>::value) {
+        const int kinds[] = {SFRD_REACT_NONE, SFRD_REACT_LINEAR, SFRD_REACT_FHN, SFRD_REACT_GRAY_SCOTT,
+                             SFRD_REACT_SCHNAKENBERG, SFRD_REACT_GIERER_MEINHARDT};
+        for (int kind : kinds) {
+            const cudaError_t e = set_smem_attrs(x2_kind_kernel<T, N, BCT>(kind), kMaxDynSmem2);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
