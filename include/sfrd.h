@@ -320,9 +320,12 @@ int sfrd_adjoint(sfrd_plan_t plan, double t0, int64_t nsteps, int64_t ckpt_every
  * count independent problems of the same dimension, species count, reaction
  * kind/parameters, dtype and time step, each with its own grid (intervals per
  * axis <= 512), boundary condition bcs[i] and coefficients alpha[i*S+s],
- * kappa[i*S+s].  One ETDRK4-P13 step of all instances is one persistent launch
- * per pass (8 in 2D, 16 in 3D) replayed from a captured CUDA graph; each
- * launch's blocks draw (instance, tile) work items, longest lines first.
+ * kappa[i*S+s].  One ETDRK4-P13 step of all instances is replayed from a
+ * captured CUDA graph: each pass (8 in 2D, 16 in 3D) is one persistent launch
+ * per group of instances that share the pass axis's length (one kernel per
+ * register-engine length, one for the shared-memory engine), the groups of a
+ * pass issued as parallel branches; each launch's blocks draw (instance, tile)
+ * work items, longest lines first.
  * Fields are passed as host arrays of count device pointers, field i laid out
  * [S][...] for instance i's grid.  Errors as for single plans. */
 typedef struct sfrd_batch_s* sfrd_batch_t;

@@ -341,7 +341,7 @@ class Solver:
 
 class Batch:
     """Many independent instances (same dim, species, reaction, dt, dtype; own grid, BC, alpha,
-    kappa) stepped together, one persistent launch per pass."""
+    kappa) stepped together, one persistent launch per pass and axis-length group."""
 
     def __init__(self, cfgs: list, dtype: str | None = None, device=None):
         import torch

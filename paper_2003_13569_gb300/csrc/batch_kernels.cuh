@@ -66,15 +66,36 @@ __device__ __forceinline__ void batch_loop(const Inst* __restrict__ insts, const
 
 namespace v2 {
 
-template <typename T, int N, int MODE>
+// KIND >= 0 (FP32 two-species batches, whose instances share one reaction): the reaction pass compiled
+// for that reaction kind only, as the single-instance length-1024 pass.
+template <typename T, int N, int MODE, int KIND = -1>
 __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>()))
     batch_x2_kernel(const BatchX<T>* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
                     double stage_frac, int* counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) XArgs<T> s_args;
     __shared__ int s_w;
-    batch_loop<true>(insts, items, nitems, counter, stage_frac, &s_args, &s_w,
-               [&](const XArgs<T>& a, const BatchItem& it) { x2_body<T, N, MODE>(a, it.bx, smem_raw); });
+    batch_loop<true>(insts, items, nitems, counter, stage_frac, &s_args, &s_w, [&](const XArgs<T>& a, const BatchItem& it) {
+        x2_body<T, N, MODE, -1, KIND>(a, it.bx, smem_raw);
+    });
+}
+
+// The length-N batched reaction pass for a batch's reaction: one kernel per two-species kind for FP32
+// (kind < 0: the kernel of every kind, which also serves one-species batches).
+template <typename T, int N>
+void (*batch_x2_for(int kind))(const BatchX<T>*, const BatchItem*, int, double, int*) {
+    if constexpr (sizeof(T) == 4) {
+        switch (kind) {
+            case SFRD_REACT_SCHNAKENBERG: return batch_x2_kernel<T, N, MODE_REACT, SFRD_REACT_SCHNAKENBERG>;
+            case SFRD_REACT_GRAY_SCOTT: return batch_x2_kernel<T, N, MODE_REACT, SFRD_REACT_GRAY_SCOTT>;
+            case SFRD_REACT_FHN: return batch_x2_kernel<T, N, MODE_REACT, SFRD_REACT_FHN>;
+            case SFRD_REACT_GIERER_MEINHARDT: return batch_x2_kernel<T, N, MODE_REACT, SFRD_REACT_GIERER_MEINHARDT>;
+            case SFRD_REACT_LINEAR: return batch_x2_kernel<T, N, MODE_REACT, SFRD_REACT_LINEAR>;
+            case SFRD_REACT_NONE: return batch_x2_kernel<T, N, MODE_REACT, SFRD_REACT_NONE>;
+            default: break;
+        }
+    }
+    return batch_x2_kernel<T, N, MODE_REACT>;
 }
 
 // PAIR: the stage passes of FP32 two-species instances on element pairs (species = item.bz), as the
@@ -143,13 +164,14 @@ cudaError_t batch_grids2(int axis, int blocks_per_sm, int sms, int nitems, int* 
 }
 
 // One launch of the length-N kernel of pass kind `axis` and `mode` on stream s, `grid` blocks.
+// xkind: the reaction kind of a two-species batch, or -1 (the x pass of every kind).
 template <typename T, int N>
 cudaError_t batch_launch2(int axis, int mode, const void* args, const BatchItem* items, int nitems, double frac,
-                          int* counter, int grid, cudaStream_t s, bool pair) {
+                          int* counter, int grid, cudaStream_t s, bool pair, int xkind) {
     const size_t smem = TileOf<T, N>::E::smem_bytes();
     if (axis == BATCH_X) {
-        batch_x2_kernel<T, N, MODE_REACT><<<grid, kThreads, smem, s>>>(static_cast<const BatchX<T>*>(args), items,
-                                                                       nitems, frac, counter);
+        batch_x2_for<T, N>(xkind)<<<grid, kThreads, smem, s>>>(static_cast<const BatchX<T>*>(args), items, nitems,
+                                                               frac, counter);
         return cudaGetLastError();
     }
     auto k = reinterpret_cast<void (*)(const BatchC<T>*, const BatchItem*, int, int*)>(
@@ -162,8 +184,12 @@ cudaError_t batch_launch2(int axis, int mode, const void* args, const BatchItem*
 template <typename T, int N>
 cudaError_t batch_prepare2() {
     const int m = (int)TileOf<T, N>::E::smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(batch_x2_kernel<T, N, MODE_REACT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+    cudaError_t e = cudaSuccess;
+    const int xkinds[] = {-1, SFRD_REACT_NONE, SFRD_REACT_LINEAR, SFRD_REACT_FHN, SFRD_REACT_GRAY_SCOTT,
+                          SFRD_REACT_SCHNAKENBERG, SFRD_REACT_GIERER_MEINHARDT};
+    for (int kind : xkinds)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_x2_for<T, N>(kind), cudaFuncAttributeMaxDynamicSharedMemorySize, m);
     void (*ks[])(const BatchC<T>*, const BatchItem*, int, int*) = {
         batch_col2_kernel<T, N, MODE_PLAIN>, batch_col2_kernel<T, N, MODE_TA>, batch_col2_kernel<T, N, MODE_TB>,
         batch_col2_kernel<T, N, MODE_TC>, batch_col2_kernel<T, N, MODE_TD>};
@@ -182,7 +208,7 @@ cudaError_t batch_prepare2() {
 #define SFRD_BATCH_INSTANTIATE(T, N)                                                                     \
     template cudaError_t batch_grids2<T, N>(int, int, int, int, int*, bool);                              \
     template cudaError_t batch_launch2<T, N>(int, int, const void*, const BatchItem*, int, double, int*, int, \
-                                             cudaStream_t, bool);                                         \
+                                             cudaStream_t, bool, int);                                    \
     template cudaError_t batch_prepare2<T, N>();
 
 }  // namespace v2

@@ -28,7 +28,7 @@ namespace v2 {
 #define SFRD_BATCH_EXTERN(T, N)                                                                                \
     extern template cudaError_t batch_grids2<T, N>(int, int, int, int, int*, bool);                             \
     extern template cudaError_t batch_launch2<T, N>(int, int, const void*, const BatchItem*, int, double, int*, \
-                                                    int, cudaStream_t, bool);                                   \
+                                                    int, cudaStream_t, bool, int);                              \
     extern template cudaError_t batch_prepare2<T, N>();
 #define SFRD_BATCH_EXTERN_ALL(T)                                                                     \
     SFRD_BATCH_EXTERN(T, 64) SFRD_BATCH_EXTERN(T, 96) SFRD_BATCH_EXTERN(T, 128) SFRD_BATCH_EXTERN(T, 200) \
@@ -287,9 +287,11 @@ static cudaError_t batch_launch_group(const BatchPlan& b, const BatchPass& ps, c
     const int grid = gr.grid[batch_mode_slot(axis, mode)];
     if (grid < 1) return cudaErrorInvalidConfiguration;
     if (gr.engine == 1) {
+        // the instances of a batch share one reaction: two-species batches take its own x-pass kernel
+        const int xkind = b.S == 2 ? b.inst[0].re.kind : -1;
         switch (gr.N) {
 #define SFRD_BATCH_CASE(N) \
-    case N: return v2::batch_launch2<T, N>(axis, mode, args, items, gr.nitems, frac, counter, grid, s, gr.pair);
+    case N: return v2::batch_launch2<T, N>(axis, mode, args, items, gr.nitems, frac, counter, grid, s, gr.pair, xkind);
             SFRD_BATCH_CASE(64) SFRD_BATCH_CASE(96) SFRD_BATCH_CASE(128) SFRD_BATCH_CASE(200)
             SFRD_BATCH_CASE(256) SFRD_BATCH_CASE(384) SFRD_BATCH_CASE(512)
 #undef SFRD_BATCH_CASE

@@ -114,6 +114,24 @@ def test_forward_transform_register_engine(dim, N, bc, dtype, S):
         assert rel_max(back[sp], u[sp]) < tol
 
 
+@pytest.mark.parametrize("kind,bc", [("none", "periodic"), ("linear", "dirichlet"), ("fhn", "neumann"),
+                                     ("gray_scott", "periodic"), ("schnakenberg", "dirichlet"),
+                                     ("gierer_meinhardt", "neumann")])
+def test_contiguous_axis_of_1024_intervals_every_reaction_kind(kind, bc):
+    """2D grids whose contiguous (x) axis has 1024 intervals: the FP32 reaction pass at that length is
+    compiled once per two-species reaction kind, so each kind runs its own kernel; a few steps against
+    the oracle on every unknown, FP64 and FP32."""
+    cfg = _cfg(2, (1024, 64), bc, kind=kind, dt=0.02)
+    lo, hi = (0.0, 1.0) if kind in ("fhn", "gray_scott") else (-0.05, 0.05)
+    u0 = _rand_fields(cfg, seed=13, lo=lo, hi=hi)
+    nsteps = 3
+    ref = oracle_solver(cfg).run(u0, 0.0, nsteps)
+    g64 = _np(sf.Solver(cfg, dtype="f64").run(u0, nsteps=nsteps))
+    assert O.rel_max(list(g64), ref) < TOL64
+    g32 = _np(sf.Solver(cfg, dtype="f32").run(u0, nsteps=nsteps))
+    assert O.rel_l2(list(g32), ref) < TOL32
+
+
 @pytest.mark.parametrize("dim,N,bc,kind", [(2, (64, 128), "periodic", "gray_scott"),
                                            (2, (128, 64), "dirichlet", "schnakenberg"),
                                            (2, (64, 64), "neumann", "fhn"),
