@@ -474,10 +474,11 @@ __global__ void __launch_bounds__(kThreads, (min_blocks<T, N, MODE>())) col2_ker
     col2_body<T, N, MODE, BCT, RAT, PAIR>(a, blockIdx.x, by, smem_raw, blockIdx.z);
 }
 
-// Lengths whose contiguous-axis pass is also compiled once per two-species reaction kind (KIND >= 0: the
+// The FP32 contiguous-axis pass is also compiled once per two-species reaction kind (KIND >= 0: the
 // reaction of that kind only, no stage save), so that the kernel holds one reaction unpacking instead of
-// all of them: at length 1024 the unrolled unpackings of every kind exceed the instruction cache.
-template <typename T, int N> struct KindSpecialised { static constexpr bool value = sizeof(T) == 4 && N == 1024; };
+// all of them: at length 1024 the unrolled unpackings of every kind exceed the instruction cache, and at
+// 256 the kernel of every kind spills under its 64-register budget where the per-kind kernels do not.
+template <typename T, int N> struct KindSpecialised { static constexpr bool value = sizeof(T) == 4; };
 
 template <typename T, int N, int MODE, int BCT = -1, int KIND = -1>
 __device__ __forceinline__ void x2_body(const XArgs<T>& a, int bx, unsigned char* smem_raw) {
