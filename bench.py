@@ -49,7 +49,11 @@ def parse():
     ap.add_argument("--err-steps", type=int, default=500,
                     help="steps after which FP32 is compared with FP64 on the GPU (the workload's whole run)")
     ap.add_argument("--repeats", type=int, default=7,
-                    help="timed regions of --steps steps each; the line reports their median")
+                    help="timed regions of --steps steps each (at least; more are taken until the regions span "
+                         "about --clock-span seconds); the line reports their median")
+    ap.add_argument("--clock-span", type=float, default=1.0,
+                    help="seconds the timed regions span at least, so that the 200 ms clock sampler lands "
+                         "samples inside them")
     ap.add_argument("--gs-steps", type=int, default=200,
                     help="steps timed on the 2D Gray-Scott 1024^2 workload, FP32 and FP64 (0: skip)")
     ap.add_argument("--gs-err-steps", type=int, default=2000,
@@ -79,6 +83,15 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def timed_regions(repeats, span_s, ms_per_step, steps, cap=1000):
+    """Number of timed regions of `steps` steps: at least `repeats`, and enough to span `span_s` seconds
+    at `ms_per_step` (the warm-up's step time; None when there was no warm-up), at most `cap`."""
+    n = max(1, repeats)
+    if ms_per_step and ms_per_step > 0 and steps > 0:
+        n = max(n, min(cap, math.ceil(span_s * 1e3 / (ms_per_step * steps))))
+    return n
 
 
 def summarise_clocks(rows, t0=None, t1=None):
@@ -278,8 +291,15 @@ def main():
     stream = solver.stream
     u0_dev = torch.as_tensor(np.stack(u0)).to(device="cuda", dtype=solver.tdtype)
     solver.load(u0_dev, 0.0)
+    w0 = torch.cuda.Event(enable_timing=True)
+    w1 = torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
     solver.advance(args.warmup)
+    w1.record(stream)
     torch.cuda.synchronize()
+    # regions: --repeats, or as many as span --clock-span seconds at the warm-up's step time (same on every rank)
+    est_ms = max_over_ranks(w0.elapsed_time(w1) / args.warmup) if args.warmup > 0 else None
+    nreg = timed_regions(args.repeats, args.clock_span, est_ms, args.steps)
 
     clocks = Clocks(local) if rank == 0 else None
     time.sleep(0.3 if clocks else 0.0)
@@ -288,7 +308,7 @@ def main():
     regions = []
     if clocks:
         clocks.mark()
-    for _ in range(max(1, args.repeats)):
+    for _ in range(nreg):
         barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -302,7 +322,8 @@ def main():
     clk = clocks.stop() if clocks else None
     ms = statistics.median(regions)
     value = dof * args.steps * world / (ms * 1e-3)
-    repeats = {"regions": len(regions), "steps_per_region": args.steps, "ms_per_step_median": ms / args.steps,
+    repeats = {"regions": len(regions), "steps_per_region": args.steps, "min_span_s": args.clock_span,
+               "ms_per_step_median": ms / args.steps,
                "ms_per_step_min": min(regions) / args.steps, "ms_per_step_max": max(regions) / args.steps,
                "value_min": dof * args.steps * world / (max(regions) * 1e-3),
                "value_max": dof * args.steps * world / (min(regions) * 1e-3)}

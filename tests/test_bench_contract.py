@@ -110,3 +110,16 @@ def test_pass_model_and_committed_traffic():
     assert bench.ncu_traffic("no_such_kernel") is None
     peak, src = bench.peaks()
     assert peak > 1000 and src in ("measured", "fallback")
+
+
+def test_timed_regions_span_the_clock_sampler():
+    """The bench times at least --repeats regions of K steps, and enough of them to span about a second
+    (the 200 ms clock sampler then lands samples inside them): 20 steps of 1.6 ms need 32 regions, 500
+    steps keep the 7 asked for, no warm-up estimate keeps --repeats, and the count is capped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.timed_regions(7, 1.0, 1.6, 20) == 32
+    assert bench.timed_regions(7, 1.0, 1.6, 500) == 7
+    assert bench.timed_regions(7, 1.0, None, 20) == 7
+    assert bench.timed_regions(0, 1.0, None, 20) == 1
+    assert bench.timed_regions(7, 1.0, 1e-6, 1) == 1000
