@@ -62,6 +62,29 @@ CASES = [((64, 64), "neumann", "fhn", 2), ((64, 128), "periodic", "gray_scott", 
          ((128,), "neumann", "fhn", 1), ((96,), "dirichlet", "gray_scott", 1), ((256,), "periodic", "schnakenberg", 1)]
 
 
+@pytest.mark.parametrize("scheme", ["p13", "cox_matthews"])
+@pytest.mark.parametrize("N,bc,dim", [((64, 128), "neumann", 2), ((96, 64), "dirichlet", 2),
+                                      ((64, 64, 64), "periodic", 3), ((128,), "neumann", 1)])
+def test_adjoint_is_the_transpose_of_the_linear_run(N, bc, dim, scheme):
+    """Dot-product test through the C ABI: with a linear reaction the checkpointed run u0 -> u_M is a
+    linear map J, and sfrd_adjoint with dl/du_M = w must return J^T w: <J v, w> = <v, J^T w> to
+    rounding, for random v, w (FP64).  With the library's diagonal linear reaction J is symmetric for
+    periodic and Dirichlet grids, where the test checks scaling and coefficients; the Neumann cases
+    (weighted DCT-I, not symmetric) also tell J from J^T."""
+    cfg = dict(_cfg(N, bc, "fhn", dim=dim, alpha=(1.5, 1.8), kappa=(0.4, 0.1), dt=0.02), scheme=scheme)
+    cfg["reaction"] = dict(kind="linear", p=[-0.7], offset=[0.0, 0.0])
+    rng = np.random.default_rng(23)
+    shp = (2,) + W.field_shape(cfg)
+    v, w = rng.standard_normal(shp), rng.standard_normal(shp)
+    nsteps, K = 5, 2
+    s = sf.Solver(cfg, dtype="f64")
+    Jv = s.run_checkpointed(v, 0.0, nsteps, K)
+    JTw = s.adjoint(torch.as_tensor(w, device=Jv.device), 0.0, nsteps, K)[0].double().cpu().numpy()
+    Jv = Jv.double().cpu().numpy()
+    lhs, rhs = float(np.sum(Jv * w)), float(np.sum(v * JTw))
+    assert abs(lhs - rhs) <= 1e-12 * float(np.linalg.norm(Jv) * np.linalg.norm(w))
+
+
 @pytest.mark.parametrize("N,bc,kind,dim", CASES)
 def test_adjoint_matches_oracle_adjoint(N, bc, kind, dim):
     cfg = _cfg(N, bc, kind, dim=dim, dt=0.02 if dim == 3 else 0.05)

@@ -554,6 +554,39 @@ def test_oracle_adjoint_matches_central_differences(bc):
         assert gr["u0"][sp_][i, j] == pytest.approx(fd, rel=1e-6, abs=1e-9)
 
 
+@pytest.mark.parametrize("bc", O.BCS)
+@pytest.mark.parametrize("scheme", ["p13", "cox_matthews"])
+def test_oracle_adjoint_is_the_transpose_of_the_linear_run(bc, scheme):
+    """Dot-product test: with a linear reaction f(u, v) = C (u, v) the run u0 -> u_M is a linear map J,
+    and the reverse sweep must apply its transpose, <J v, w> = <v, J^T w>, to rounding, for random v, w.
+    C couples the species non-symmetrically and the species have their own orders and diffusivities, so
+    J is not symmetric for any boundary condition and a transposed operand is detected (checked below)."""
+    g = O.Grid((8, 6), (0.0, 0.0), (3.0, 4.0))
+    C = [[-0.7, 0.3], [-0.2, -0.5]]
+
+    def f(w_, t):
+        return [C[0][0] * w_[0] + C[0][1] * w_[1], C[1][0] * w_[0] + C[1][1] * w_[1]]
+
+    def J(w_, t):
+        return [[C[r][c] * np.ones_like(w_[0]) for c in range(2)] for r in range(2)]
+    prob = O.Problem(g, bc, [1.5, 1.8], [0.4, 0.1], 0.05, f, dreaction=J)
+    s = O.ETDRK4P13(prob, scheme=scheme)
+    rng = np.random.default_rng(21)
+    shp = g.shape(bc)
+    v = [rng.standard_normal(shp) for _ in range(2)]
+    w = [rng.standard_normal(shp) for _ in range(2)]
+    M = 4
+    Jv = s.run(v, 0.0, M)
+    JTw = O.adjoint_run(s, v, 0.0, M, w)["u0"]
+    lhs = sum(float(np.sum(a * b)) for a, b in zip(Jv, w))
+    rhs = sum(float(np.sum(a * b)) for a, b in zip(v, JTw))
+    scale = np.sqrt(sum(float(np.sum(a * a)) for a in Jv) * sum(float(np.sum(b * b)) for b in w))
+    assert abs(lhs - rhs) <= 1e-13 * scale
+    # a transposed operand would break it: the forward map applied in place of its transpose
+    Jw = s.run(w, 0.0, M)
+    assert abs(sum(float(np.sum(a * b)) for a, b in zip(v, Jw)) - lhs) > 1e-6 * scale
+
+
 # --------------------------------------------------------------------------
 # The Cox-Matthews variant (exact exponentials, Section 4's reference scheme)
 # --------------------------------------------------------------------------
