@@ -25,7 +25,7 @@ def _workload(name):
 
 def test_there_are_stored_runs():
     names = [os.path.basename(f)[len("fullrun_"):-len(".npz")] for f in FILES]
-    assert "schnak128" in names
+    assert {"schnak128", "schnak256", "gs1024"} <= set(names)
     assert sum(n.startswith("gm") for n in names) == len(W.GM_SIDES) * len(W.GM_BCS)
 
 
